@@ -1,0 +1,230 @@
+/*
+ * to.h -- C ABI of the GB300 batched trajectory-optimisation library (libto.so).
+ *
+ * The library solves many independent instances of the paper's finite-horizon
+ * discrete optimal control problem (Sec. II, Eq. 1)
+ *
+ *     min_{X,U}  sum_{k=0}^{T-1} l_k(x_k, u_k) + l_T(x_T)
+ *     s.t.       x_{k+1} = f_k(x_k, u_k),  k = 0..T-1,   x_0 = x_init,
+ *
+ * one per initial state, with iLQR: a DDP backward pass without second-order
+ * dynamics terms whose value gradient V_x is also returned (Sec. II), Cholesky
+ * of Q_uu with the LM term Q_uu + mu I only as a guard (Sec. IV-B),
+ * eigenvalue clipping of the state- and control-cost Hessians,
+ * S' = max(S, eps), Q_psd = sym(W diag(S') W^T) (Sec. IV-B), a parallel line
+ * search over step sizes alpha_j = decay^j, and a fixed per-instance iteration
+ * budget (Sec. IV-A).  The warm start is zero controls, caller-given controls,
+ * or the actor policy rolled out through the dynamics (Sec. II).  The control
+ * bound |u| <= u_max of Eq. 1 is not supported (u_max must be +inf).
+ *
+ * Conventions
+ *   - Every function returns TO_OK (0) or a negative TO_ERR_* code; the
+ *     message of the last error on the calling thread is tolast_error().
+ *   - Host arrays are instance-major, row-major, float64.  The caller owns
+ *     every host pointer; the library copies what it needs before returning
+ *     (or, for asynchronous calls, before the call's stream work starts).
+ *   - The library owns all device memory it allocates; tofree_batch and
+ *     todestroy_problem release it.  Device pointers passed in by the caller
+ *     stay owned by the caller.
+ *   - Per-instance outcomes are reported in status[], not in return codes.
+ *   - Horizons shorter than T_max are padded in outputs: U with 0, X with x_T
+ *     repeated, V_x with 0.
+ *   - The library is single-GPU: every call runs on the device current on the
+ *     calling thread when the problem was created.
+ */
+#ifndef TO_H
+#define TO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct to_problem_s* to_problem;
+typedef struct to_batch_s* to_batch;
+
+/* systems (Sec. V-A: point mass, manipulators; Sec. V-D: quadruped-shaped) */
+enum {
+  TO_SYS_POINTMASS2D = 1, /* n=4 [px,py,vx,vy], m=2, explicit Euler              */
+  TO_SYS_PLANAR3 = 2,     /* planar 3-link arm, n=6, m=3, semi-implicit Euler     */
+  TO_SYS_ARM7 = 3,        /* 7-DoF serial arm, n=14, m=7, semi-implicit Euler     */
+  TO_SYS_QUAD18 = 4       /* 6 virtual base joints + 4x3 legs, n=36, m=12, contact */
+};
+
+/* arithmetic of the solve */
+enum {
+  TO_FP64 = 0, /* every step in float64                                        */
+  TO_MIXED = 1 /* float32 rollouts, derivatives and Riccati products; float64
+                  Q_uu Cholesky, pivot test, refinement residual and the
+                  line-search cost comparison; the cost is accumulated as a
+                  compensated float32 pair (about 48 significant bits)        */
+};
+
+/* return codes */
+enum {
+  TO_OK = 0,
+  TO_ERR_ARG = -1,      /* malformed argument (message says which)            */
+  TO_ERR_CUDA = -2,     /* a CUDA runtime call failed                         */
+  TO_ERR_BUDGET = -3,   /* request exceeds the HBM budget / batch capacity    */
+  TO_ERR_TIMEOUT = -4,  /* a bounded wait ran out                             */
+  TO_ERR_NOTREADY = -5, /* result not available yet (serving)                 */
+  TO_ERR_UNSUPPORTED = -6
+};
+
+/* per-instance status (low 4 bits) and flags */
+enum {
+  TO_ST_CONVERGED = 1, /* relative cost decrease fell below tol_rel             */
+  TO_ST_MAX_ITER = 2,  /* iteration budget used (or forced sequence ended)      */
+  TO_ST_LS_FAIL = 3,   /* no step size decreased the cost; iterate kept         */
+  TO_ST_NONFINITE = 4, /* the cost or a Cholesky became non-finite              */
+  TO_ST_TIMEOUT = 5,   /* a bounded device wait ran out                         */
+  TO_ST_FLAG_REG = 16  /* some Q_uu failed the pivot test and got mu I added    */
+};
+
+/*
+ * Problem description.  params is the flat float64 vector of the system:
+ *
+ * TO_SYS_POINTMASS2D:
+ *   [0] dt  [1] w_u  [2] bump amplitude  [3] bump sigma  [4] nb (<= 8)
+ *   [5 .. 5+2nb) bump centres (x, y)  [5+2nb] w_pT  [6+2nb] w_vT
+ *   l_k = w_u |u|^2 + sum_b amp exp(-|p - c_b|^2 / (2 sigma^2))
+ *   l_T = w_pT |p|^2 + w_vT |v|^2
+ *
+ * Rigid-body systems (TO_SYS_PLANAR3, TO_SYS_ARM7, TO_SYS_QUAD18):
+ *   header  [0] dt  [1..3] gravity vector (world)  [4] N joints  [5] a0 (first
+ *           actuated joint; m = N - a0)  [6] n_sub (semi-implicit Euler
+ *           substeps of dt/n_sub per knot, 0 means 1)  [7] 0
+ *   body i  at 8 + 16 i: [0] parent (-1 root) [1] joint type (0 Rx, 1 Ry,
+ *           2 Rz, 3 Px, 4 Py, 5 Pz) [2..4] joint offset in the parent frame
+ *           [5] mass [6..8] centre of mass [9..11] diagonal inertia about the
+ *           centre of mass [12..15] 0
+ *   cost block at C = 8 + 16 N:
+ *   PLANAR3 (gravity in the xy plane, joints Rz, links along +x):
+ *     [C] w_tau [C+1] bump amplitude [C+2] sigma [C+3] nb (<= 2)
+ *     [C+4..7] bump centres [C+8..9] target [C+10] w_ee [C+11] w_vT
+ *     [C+12] end-effector body [C+13..15] end-effector point in that body
+ *     l_k = w_tau |u|^2 + sum_b amp exp(-|ee(q) - c_b|^2 / (2 sigma^2))
+ *     l_T = w_ee |ee(q) - target|^2 + w_vT |qd|^2
+ *   ARM7:
+ *     [C] w_tau [C+1] w_v [C+2..4] target [C+5] w_ee [C+6] w_vT
+ *     [C+7] end-effector body [C+8..10] end-effector point
+ *     l_k = w_tau |u|^2 + w_v |qd|^2,  l_T = w_ee |ee(q) - target|^2 + w_vT |qd|^2
+ *   QUAD18 (base joints Px Py Pz Rz Ry Rx, legs attached to body 5):
+ *     [C] w_tau [C+1] z_nom [C+2] w_z [C+3] w_rpy [C+4] w_vx [C+5] vx target
+ *     [C+6] terminal scale [C+7] contact stiffness k [C+8] damping d
+ *     [C+9] softplus beta [C+10] n_feet (4) then per foot: body, point (3)
+ *     contact force at each foot (world): F_z = k softplus_beta(-z)
+ *       - d sigmoid(-beta z) zdot,  F_xy = -d sigmoid(-beta z) pdot_xy
+ *     l_k = w_z (z - z_nom)^2 + w_rpy |(yaw,pitch,roll)|^2 + w_vx (xdot - vx*)^2
+ *           + w_tau |u|^2,   l_T = scale * (state terms of l_k)
+ *
+ * actor_w (optional, float32): W1[256x36] b1[256] W2[256x256] b2[256]
+ * W3[12x256] b3[12], u = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3; only
+ * TO_SYS_QUAD18 accepts it.  NULL selects the zero-control warm start.
+ */
+typedef struct {
+  int sys;
+  int n, m;          /* must match the system                                 */
+  int T_max;         /* largest horizon any solve of this problem will use    */
+  double dt;         /* must equal params[0]                                  */
+  const double* params;
+  size_t n_params;
+  const float* actor_w;
+  size_t n_actor_w;
+  double u_max;      /* must be +inf                                          */
+} to_problem_desc;
+
+typedef struct {
+  int max_iter;           /* iteration budget per instance (Sec. IV-A)         */
+  double tol_rel;         /* stop when (J_old - J_new) / |J_old| < tol_rel     */
+  double eps_clip;        /* eigenvalue floor eps (Sec. IV-B)                  */
+  int n_alpha;            /* number of step sizes L (1..32)                    */
+  double alpha_decay;     /* alpha_j = alpha_decay^j                           */
+  int prec;               /* TO_FP64 or TO_MIXED                               */
+  int refine;             /* mixed mode: 1 = one FP64-residual refinement step of
+                             the gain solve, 0 = none                          */
+  const int* forced_alpha;/* test hook, host B x max_iter or NULL: iteration i of
+                             instance b takes step index forced_alpha[b*max_iter+i]
+                             with no test; -1 ends that instance's run          */
+  int want_vx;            /* 1: one more backward pass at the returned iterate
+                             gives V_x and the gains K, k there                */
+  size_t hbm_budget_bytes;/* 0 = no limit; else tocreate_batch / tosolve_batch
+                             refuse a workspace larger than this (TO_ERR_BUDGET) */
+  int group_lanes;        /* threads per instance (4..256); 0 = autotuned       */
+  int groups_per_block;   /* instances resident per CTA; 0 = autotuned          */
+  int profile_phases;     /* 1: accumulate per-phase clock64 cycles (tracing;
+                             see toget_phase_cycles); 0 = off                 */
+} to_solver_opts;
+
+/* Defaults: max_iter 100, tol_rel 1e-8, eps_clip 1e-8, n_alpha 16,
+ * alpha_decay 0.5, TO_MIXED, refine 1, no forcing, want_vx 0, no budget,
+ * autotuned launch shape. */
+void to_default_opts(to_solver_opts* opts);
+
+/* Validate the description, parse params into the system's device layout and
+ * upload it (plus the actor weights).  Errors: TO_ERR_ARG (shape, layout or a
+ * system whose joint structure the GPU model does not cover), TO_ERR_CUDA. */
+int tocreate_problem(const to_problem_desc* desc, to_problem* out);
+void todestroy_problem(to_problem p);
+
+/* Allocate the device workspace of a batch able to hold B_max instances whose
+ * horizons sum (over T+1) to at most knots_max.  Reusing one batch object for
+ * many solves keeps allocation out of the solve.  Errors: TO_ERR_ARG,
+ * TO_ERR_BUDGET (workspace above opts->hbm_budget_bytes), TO_ERR_CUDA. */
+int tocreate_batch(to_problem p, int B_max, long long knots_max, const to_solver_opts* opts, to_batch* out);
+void tofree_batch(to_batch b);
+
+/* Solve B instances.  x0: host B x n; T: host B horizons in [1, T_max];
+ * U_init: host B x T_max x m initial controls or NULL (zero controls, or the
+ * actor warm start when the problem has actor weights).  The work is enqueued
+ * on cuda_stream (a cudaStream_t, NULL = the legacy default stream) and the
+ * call returns once the host inputs are copied.  If *out is NULL a batch sized
+ * for this call is created and returned; otherwise *out is reused and must
+ * have enough capacity.  Errors: TO_ERR_ARG, TO_ERR_BUDGET, TO_ERR_CUDA. */
+int tosolve_batch(to_problem p, int B, const double* x0, const int* T, const double* U_init,
+                  const to_solver_opts* opts, void* cuda_stream, to_batch* out);
+
+/* Same solve with inputs already in device memory: d_x0 (B x n float64),
+ * d_T (B int32, each in [1, T_max]), d_U_init (B x T_max x m float64 or NULL),
+ * d_forced (B x max_iter int32 or NULL; replaces opts->forced_alpha).  Sum of
+ * (T+1) must not exceed the batch's knots_max (checked on the device: an
+ * overflowing solve marks every instance TO_ST_NONFINITE and computes
+ * nothing).  Nothing is copied between host and device. */
+int tosolve_batch_device(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U_init,
+                         const int* d_forced, const to_solver_opts* opts, void* cuda_stream);
+
+/* Copy results of the last solve to the host (synchronises the batch's
+ * stream).  X: B x (T_max+1) x n, U: B x T_max x m, J, iters, status: B;
+ * Vx: B x (T_max+1) x n and K: B x T_max x m x n (need want_vx; may be NULL);
+ * any output pointer may be NULL.  T_max is the problem's. */
+int toget_trajectories(to_batch b, double* X, double* U, double* J, int* iters, int* status, double* Vx,
+                       double* K);
+
+/* Per-iteration record of the last solve: accepted step index (B x max_iter,
+ * -1 after the last iteration) and cost (B x (max_iter+1), J_hist[b][0] is the
+ * warm-start cost).  Either pointer may be NULL. */
+int toget_history(to_batch b, int* alpha_idx, double* J_hist);
+
+/* Device-resident results of the last solve (no copy): J (float64, B),
+ * iters and status (int32, B), in the batch's own memory. */
+int toget_device_results(to_batch b, const double** d_J, const int** d_iters, const int** d_status);
+
+/* Tracing: SM cycles the last solve (run with profile_phases = 1) spent per
+ * phase, summed over warps: [0] queue / bookkeeping, [1] backward: knot
+ * staging + derivatives, [2] backward: V A, V B and the Q terms, [3] backward:
+ * Cholesky + gain solve, [4] backward: value update, [5] forward rounds
+ * (parallel line search, warm-start rollout), [6] 0, [7] total.  out must
+ * hold 8 values. */
+int toget_phase_cycles(to_batch b, unsigned long long* out);
+
+/* Number of kernels the last tosolve_batch / tosolve_batch_device launched. */
+int tolast_launch_count(to_batch b);
+
+const char* tolast_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TO_H */

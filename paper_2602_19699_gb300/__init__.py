@@ -1,0 +1,286 @@
+"""Python binding of libto.so, the GB300 batched iLQR library (include/to.h).
+
+The functions keep the C names (``tocreate_problem``, ``tosolve_batch``,
+``toget_trajectories`` ...) and only marshal arguments: every step of the
+solve runs in the CUDA kernels of the shared library.  There is no CPU
+fallback: calling into the library without a built ``libto.so`` or without a
+CUDA device raises.
+
+``Solver`` is a small convenience wrapper (one problem + one reusable batch).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libto.so")
+
+TO_SYS_POINTMASS2D, TO_SYS_PLANAR3, TO_SYS_ARM7, TO_SYS_QUAD18 = 1, 2, 3, 4
+TO_FP64, TO_MIXED = 0, 1
+TO_OK, TO_ERR_ARG, TO_ERR_CUDA, TO_ERR_BUDGET, TO_ERR_TIMEOUT, TO_ERR_NOTREADY, TO_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+TO_ST_CONVERGED, TO_ST_MAX_ITER, TO_ST_LS_FAIL, TO_ST_NONFINITE, TO_ST_TIMEOUT, TO_ST_FLAG_REG = 1, 2, 3, 4, 5, 16
+
+
+class ToError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libto error {code}: {msg}")
+        self.code = code
+
+
+class to_problem_desc(C.Structure):
+    _fields_ = [("sys", C.c_int), ("n", C.c_int), ("m", C.c_int), ("T_max", C.c_int), ("dt", C.c_double),
+                ("params", C.POINTER(C.c_double)), ("n_params", C.c_size_t),
+                ("actor_w", C.POINTER(C.c_float)), ("n_actor_w", C.c_size_t), ("u_max", C.c_double)]
+
+
+class to_solver_opts(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("tol_rel", C.c_double), ("eps_clip", C.c_double), ("n_alpha", C.c_int),
+                ("alpha_decay", C.c_double), ("prec", C.c_int), ("refine", C.c_int),
+                ("forced_alpha", C.POINTER(C.c_int)), ("want_vx", C.c_int), ("hbm_budget_bytes", C.c_size_t),
+                ("group_lanes", C.c_int), ("groups_per_block", C.c_int), ("profile_phases", C.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    from . import nvcc_build as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """The loaded libto.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libto.so is not built ({LIB_PATH}); run paper_2602_19699_gb300.build()")
+            L = C.CDLL(LIB_PATH)
+            vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+            L.tocreate_problem.argtypes = [C.POINTER(to_problem_desc), C.POINTER(vp)]
+            L.todestroy_problem.argtypes = [vp]
+            L.todestroy_problem.restype = None
+            L.tocreate_batch.argtypes = [vp, i, ll, C.POINTER(to_solver_opts), C.POINTER(vp)]
+            L.tofree_batch.argtypes = [vp]
+            L.tofree_batch.restype = None
+            L.tosolve_batch.argtypes = [vp, i, vp, vp, vp, C.POINTER(to_solver_opts), vp, C.POINTER(vp)]
+            L.tosolve_batch_device.argtypes = [vp, i, vp, vp, vp, vp, C.POINTER(to_solver_opts), vp]
+            L.toget_trajectories.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+            L.toget_history.argtypes = [vp, vp, vp]
+            L.toget_device_results.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+            L.tolast_launch_count.argtypes = [vp]
+            L.toget_phase_cycles.argtypes = [vp, vp]
+            L.tolast_error.restype = C.c_char_p
+            L.to_default_opts.argtypes = [C.POINTER(to_solver_opts)]
+            L.to_default_opts.restype = None
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return ["to_default_opts", "tocreate_problem", "todestroy_problem", "tocreate_batch", "tofree_batch",
+            "tosolve_batch", "tosolve_batch_device", "toget_trajectories", "toget_history",
+            "toget_device_results", "tolast_launch_count", "toget_phase_cycles", "tolast_error"]
+
+
+def tolast_error() -> str:
+    return lib().tolast_error().decode()
+
+
+def _check(rc):
+    if rc != TO_OK:
+        raise ToError(rc, tolast_error())
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def to_default_opts(**overrides) -> to_solver_opts:
+    o = to_solver_opts()
+    lib().to_default_opts(C.byref(o))
+    for k, v in overrides.items():
+        if k == "forced_alpha":
+            raise ValueError("pass forced_alpha to tosolve_batch")
+        setattr(o, k, v)
+    return o
+
+
+class Problem:
+    """Handle of a created problem (keeps the host parameter copy alive)."""
+
+    def __init__(self, handle, sys, n, m, T_max):
+        self.handle, self.sys, self.n, self.m, self.T_max = handle, sys, n, m, T_max
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.todestroy_problem(self.handle)
+            self.handle = None
+
+
+class Batch:
+    def __init__(self, handle, problem):
+        self.handle, self.problem = handle, problem
+        self.B = 0
+        self.max_iter = 0
+        self.want_vx = 0
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tofree_batch(self.handle)
+            self.handle = None
+
+
+def tocreate_problem(sys, params, T_max, actor_w=None, n=None, m=None, dt=None) -> Problem:
+    from .workload import NM
+    n0, m0 = NM.get(sys, (0, 0))
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    d = to_problem_desc()
+    d.sys = sys
+    d.n = n0 if n is None else n
+    d.m = m0 if m is None else m
+    d.T_max = int(T_max)
+    d.dt = float(p[0]) if dt is None else dt
+    d.params = p.ctypes.data_as(C.POINTER(C.c_double))
+    d.n_params = p.size
+    aw = None
+    if actor_w is not None:
+        aw = np.ascontiguousarray(actor_w, dtype=np.float32)
+        d.actor_w = aw.ctypes.data_as(C.POINTER(C.c_float))
+        d.n_actor_w = aw.size
+    d.u_max = float("inf")
+    h = C.c_void_p()
+    _check(lib().tocreate_problem(C.byref(d), C.byref(h)))
+    return Problem(h, sys, d.n, d.m, d.T_max)
+
+
+def tocreate_batch(problem: Problem, B_max: int, knots_max: int, opts: to_solver_opts | None = None) -> Batch:
+    h = C.c_void_p()
+    _check(lib().tocreate_batch(problem.handle, int(B_max), int(knots_max), C.byref(opts) if opts else None,
+                                C.byref(h)))
+    return Batch(h, problem)
+
+
+def tosolve_batch(problem: Problem, x0, T, U_init=None, opts: to_solver_opts | None = None, stream=None,
+                  batch: Batch | None = None, forced_alpha=None) -> Batch:
+    """Solve with host inputs; returns the (possibly new) batch.  Asynchronous on ``stream``."""
+    x0 = np.ascontiguousarray(np.atleast_2d(x0), dtype=np.float64)
+    B = x0.shape[0]
+    T = np.ascontiguousarray(np.broadcast_to(np.asarray(T), (B,)), dtype=np.int32)
+    opts = opts if opts is not None else to_default_opts()
+    fa = None
+    if forced_alpha is not None:
+        fa = np.ascontiguousarray(forced_alpha, dtype=np.int32)
+        assert fa.shape == (B, opts.max_iter)
+        opts.forced_alpha = fa.ctypes.data_as(C.POINTER(C.c_int))
+    else:
+        opts.forced_alpha = None
+    U = None
+    if U_init is not None:
+        U = np.ascontiguousarray(U_init, dtype=np.float64)
+        assert U.shape == (B, problem.T_max, problem.m)
+    h = C.c_void_p(batch.handle.value if batch is not None else None)
+    rc = lib().tosolve_batch(problem.handle, B, _ptr(x0), _ptr(T), _ptr(U), C.byref(opts),
+                             C.c_void_p(stream) if stream else None, C.byref(h))
+    opts.forced_alpha = None
+    _check(rc)
+    if batch is None:
+        batch = Batch(h, problem)
+    batch.B, batch.max_iter, batch.want_vx = B, opts.max_iter, opts.want_vx
+    return batch
+
+
+def tosolve_batch_device(batch: Batch, B: int, d_x0: int, d_T: int, d_U_init: int | None = None,
+                         d_forced: int | None = None, opts: to_solver_opts | None = None, stream=None):
+    """Solve with device-resident inputs (raw device pointers, e.g. torch ``data_ptr()``)."""
+    opts = opts if opts is not None else to_default_opts()
+    opts.forced_alpha = None
+    _check(lib().tosolve_batch_device(batch.handle, int(B), C.c_void_p(d_x0), C.c_void_p(d_T),
+                                      C.c_void_p(d_U_init) if d_U_init else None,
+                                      C.c_void_p(d_forced) if d_forced else None, C.byref(opts),
+                                      C.c_void_p(stream) if stream else None))
+    batch.B, batch.max_iter, batch.want_vx = B, opts.max_iter, opts.want_vx
+
+
+def toget_trajectories(batch: Batch, X=True, U=True, Vx=False, K=False) -> dict:
+    p = batch.problem
+    B = batch.B
+    out = {
+        "J": np.empty(B), "iters": np.empty(B, np.int32), "status": np.empty(B, np.int32),
+        "X": np.empty((B, p.T_max + 1, p.n)) if X else None,
+        "U": np.empty((B, p.T_max, p.m)) if U else None,
+        "Vx": np.empty((B, p.T_max + 1, p.n)) if Vx else None,
+        "K": np.empty((B, p.T_max, p.m, p.n)) if K else None,
+    }
+    _check(lib().toget_trajectories(batch.handle, _ptr(out["X"]), _ptr(out["U"]), _ptr(out["J"]),
+                                    _ptr(out["iters"]), _ptr(out["status"]), _ptr(out["Vx"]), _ptr(out["K"])))
+    return out
+
+
+def toget_history(batch: Batch) -> tuple[np.ndarray, np.ndarray]:
+    B, mi = batch.B, batch.max_iter
+    a = np.empty((B, max(mi, 1)), np.int32)
+    j = np.empty((B, mi + 1))
+    _check(lib().toget_history(batch.handle, _ptr(a), _ptr(j)))
+    return a[:, :mi], j
+
+
+def toget_device_results(batch: Batch) -> tuple[int, int, int]:
+    J, it, st = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    _check(lib().toget_device_results(batch.handle, C.byref(J), C.byref(it), C.byref(st)))
+    return J.value, it.value, st.value
+
+
+PHASES = ("bookkeeping", "bwd_derivs", "bwd_products", "bwd_chol_gains", "bwd_update", "line_search", "commit")
+
+
+def toget_phase_cycles(batch: Batch) -> dict:
+    out = np.zeros(8, np.uint64)
+    _check(lib().toget_phase_cycles(batch.handle, _ptr(out)))
+    d = {k: int(v) for k, v in zip(PHASES, out[:7])}
+    d["total"] = int(out[7])
+    return d
+
+
+def tolast_launch_count(batch: Batch) -> int:
+    return int(lib().tolast_launch_count(batch.handle))
+
+
+class Solver:
+    """One problem and a reusable batch: ``Solver(prob).solve(x0, T, ...)`` returns a result dict."""
+
+    def __init__(self, prob, T_max=None, prec=TO_MIXED, B_max=None, knots_max=None, **opt_overrides):
+        self.prob = prob
+        self.T_max = int(T_max or 400)
+        self.problem = tocreate_problem(prob.sys, prob.params, self.T_max, actor_w=prob.actor_w)
+        self.opts = to_default_opts(prec=prec, **opt_overrides)
+        self.batch = None
+        self._cap = (0, 0, TO_MIXED)
+        if B_max is not None:
+            self._ensure(B_max, knots_max or B_max * (self.T_max + 1), prec)
+
+    def _ensure(self, B, knots, prec):
+        cB, cK, cP = self._cap
+        if self.batch is None or B > cB or knots > cK or (prec == TO_FP64 and cP != TO_FP64):
+            B, knots = max(B, cB), max(knots, cK)
+            p = TO_FP64 if (prec == TO_FP64 or cP == TO_FP64) else TO_MIXED
+            self.batch = None
+            self.batch = tocreate_batch(self.problem, B, knots, to_default_opts(prec=p))
+            self._cap = (B, knots, p)
+
+    def solve(self, x0, T, U_init=None, forced_alpha=None, want=("X", "U"), history=True, **overrides):
+        opts = to_default_opts(**{f: getattr(self.opts, f) for f, _ in to_solver_opts._fields_ if f != "forced_alpha"})
+        for k, v in overrides.items():
+            setattr(opts, k, v)
+        Ts = np.broadcast_to(np.asarray(T), (np.atleast_2d(x0).shape[0],))
+        self._ensure(len(Ts), int(np.sum(Ts + 1)), opts.prec)
+        self.batch = tosolve_batch(self.problem, x0, T, U_init, opts, batch=self.batch, forced_alpha=forced_alpha)
+        r = toget_trajectories(self.batch, X="X" in want, U="U" in want, Vx="Vx" in want, K="K" in want)
+        if history:
+            r["alpha_hist"], r["J_hist"] = toget_history(self.batch)
+        return r

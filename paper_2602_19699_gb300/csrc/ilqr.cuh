@@ -1,0 +1,666 @@
+// Batched iLQR solver kernel, generic over the system and the arithmetic.
+//
+// One group of G threads owns one OCP instance (Sec. II, Eq. 1) and runs the
+// whole iteration for it:
+//   backward pass  (Sec. II: DDP backward pass without second-order dynamics
+//                   terms; Sec. IV-B: eigenvalue-clipped cost Hessians and the
+//                   Cholesky of Q_uu with mu I only when the pivot test fails)
+//   line search    (step sizes alpha_j = decay^j evaluated LW at a time, one
+//                   per lane, each rolled out into its own trajectory slot; the
+//                   smallest j with J(alpha_j) < J_old is accepted and its slot
+//                   becomes the current iterate, so nothing is rolled out
+//                   twice; a further round of LW runs only if no step in the
+//                   round decreased the cost)
+//   bookkeeping    (fixed iteration budget per instance, Sec. IV-A; relative
+//                   cost-decrease test)
+// The grid is persistent: a group that finishes an instance takes the next
+// one from a queue ordered by horizon (longest first), so instances with
+// uneven horizons and iteration counts share one launch.  Groups that share a
+// warp run warp-uniform control flow; per-group work is predicated.  Every
+// phase prefetches the next knot record into registers while the current
+// knot computes.
+//
+// Arithmetic: R = double (FP64 mode) or float (mixed mode).  In mixed mode
+// rollouts, derivatives and Riccati products are float32; the Q_uu Cholesky
+// and its pivot test and the residual of the one-step refinement of the gain
+// solve are float64; the cost is accumulated as a compensated float32 pair
+// (about 48 significant bits) and compared in float64.
+#pragma once
+#include "common.cuh"
+
+namespace to {
+
+constexpr int kMaxAlpha = 32;
+constexpr int kLsWidth = 16;                 // most step sizes tried at once
+constexpr int kMaxSlots = kLsWidth + 1;      // trajectory slots per knot for the widest groups
+
+struct SolveArgs {
+  int B, T_max, max_iter, n_alpha, refine, want_vx;
+  double tol, eps;
+  double alpha_d[kMaxAlpha];   // alpha_j = decay^j
+  float alpha_f[kMaxAlpha];
+  const double* x0;         // B x n
+  const int* T;             // B
+  const double* U_init;     // B x T_max x m or null
+  const int* forced;        // B x max_iter or null
+  const long long* toff;    // B: first knot record of each instance
+  const int* order;         // B: instance indices, longest horizon first
+  int* queue;               // work counter
+  void* traj;               // knot records [x | u | pad] (R), (LW + 1) slots per knot
+  void* gains;              // gain records [K (m x n) | k (m) | pad] (R)
+  double* vx;               // knots x n, or null
+  double* J_out;
+  int* iters_out;
+  int* status_out;
+  int* slot_out;            // B: trajectory slot holding the returned iterate
+  int* ahist;               // B x max_iter
+  double* Jhist;            // B x (max_iter + 1)
+  const void* params;       // the system's parameter struct in the kernel's precision
+  const float* actor_w;     // actor weights or null
+  const int* err;           // set by the prepare kernel on malformed input
+  unsigned long long* prof; // 8 per-phase cycle counters, or null (tracing off)
+};
+
+// per-phase clock64 accounting (tracing); one timer thread per warp / CTA
+#define TO_TICK(ph)                                                                  \
+  if (a.prof) {                                                                      \
+    const long long t_ = clock64();                                                  \
+    if (timer) atomicAdd(a.prof + (ph), (unsigned long long)(t_ - tlast));           \
+    tlast = t_;                                                                      \
+  }
+
+template <class Sys, class R>
+struct Layout {
+  static constexpr int n = Sys::n, m = Sys::m;
+  static constexpr int kVec = 16 / (int)sizeof(R);
+  static constexpr int RS = (n + m + kVec - 1) / kVec * kVec;
+  static constexpr int GS = (m * (n + 1) + kVec - 1) / kVec * kVec;
+};
+
+// cost accumulator: plain float64, or a compensated float32 pair (two-sum)
+template <class R> struct Acc;
+template <> struct Acc<double> {
+  double s = 0;
+  TO_DEV void add(double v) { s += v; }
+  TO_DEV double value() const { return s; }
+};
+template <> struct Acc<float> {
+  float hi = 0.f, lo = 0.f;
+  TO_DEV void add(float v) {
+    const float t = hi + v;
+    const float bv = t - hi;
+    lo += (hi - (t - bv)) + (v - bv);
+    hi = t;
+  }
+  TO_DEV double value() const { return (double)hi + (double)lo; }
+};
+
+// per-group shared-memory workspace
+template <class Sys, class R>
+struct Work {
+  static constexpr int n = Sys::n, m = Sys::m;
+  double Quu[m * m];
+  double L[m * m];       // float64 Cholesky factor of Q_uu (+ mu I)
+  double mu;
+  double red;
+  R Lf[m * m];           // the factor rounded to R, unit diagonal scaled: Lf[jj] = 1 / L_jj
+  R V[n * n];            // V_xx, then Q_xx, then the new V_xx (in place)
+  R v[n];                // V_x
+  R A[n * n];
+  R Bm[n * m];
+  R VA[n * n];           // V A; scratch of the derivatives
+  R VB[n * m];
+  R lxx[n * n];
+  R Qux[m * n];
+  R Qx[n];
+  R Qu[m];
+  R lx[n];
+  R lu[m];
+  R luu[m * m];
+  R xk[n];               // staged knot record: x_k, u_k (adjacent)
+  R uk[m];
+  R K[m * n];            // gains K_k, k_k (adjacent)
+  R kf[m];
+  int flag;              // Cholesky: 0 ok, 1 regularised, 2 failed
+  int sel;
+  int wslot;             // slot of the accepted line-search candidate
+};
+
+enum { M_IDLE = 0, M_NEW, M_RUN, M_FINAL, M_DRAINED };
+
+template <class Sys, class R, int G>
+struct Solver {
+  static constexpr int n = Sys::n, m = Sys::m;
+  static constexpr int RS = Layout<Sys, R>::RS, GS = Layout<Sys, R>::GS;
+  static constexpr int NF = n + m + m * (n + 1);          // forward record: x, u, K, k
+  static constexpr int PF = (NF + G - 1) / G;             // prefetch registers per lane (forward)
+  static constexpr int PB = (n + m + G - 1) / G;          // prefetch registers per lane (backward)
+  static constexpr int LW = G < kLsWidth ? G : kLsWidth;   // step sizes per line-search round
+  static constexpr int NS = LW + 1;                        // trajectory slots per knot
+  static constexpr int kRounds = (kMaxAlpha + LW - 1) / LW; // most line-search rounds
+  typedef typename Sys::template ParamsT<R> Params;
+  typedef Work<Sys, R> W;
+
+  // ------------------------------------------------------------------------
+  // Cholesky of Q_uu in float64 with the pivot test  d_j > 1e-12 max|diag|;
+  // on failure mu I is added, mu = 1e-6 max|diag| growing x10 (Sec. IV-B's
+  // Levenberg-Marquardt term, used only as this guard).  One thread; the
+  // reciprocal pivots come from rsqrt, so there is no float64 division.
+  // ------------------------------------------------------------------------
+  TO_DEV static bool chol(const double* A, double shift, double delta, double* L) {
+    for (int j = 0; j < m; ++j) {
+      double s = A[j * m + j] + shift;
+      for (int k = 0; k < j; ++k) s -= L[j * m + k] * L[j * m + k];
+      if (!(s > delta)) return false;
+      const double r = rsqrt(s);
+      L[j * m + j] = r;                      // stores 1 / L_jj
+      for (int i = j + 1; i < m; ++i) {
+        double t = A[i * m + j];
+        for (int k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
+        L[i * m + j] = t * r;
+      }
+    }
+    return true;
+  }
+  TO_DEV static void chol_guarded(W& w) {
+    double mx = 0;
+    for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(w.Quu[i * m + i]));
+    w.mu = 0;
+    w.flag = 2;
+    if (!(mx > 0) || !isfinite(mx)) return;
+    const double delta = 1e-12 * mx;
+    if (chol(w.Quu, 0.0, delta, w.L)) {
+      w.flag = 0;
+    } else {
+      double mu = 1e-6 * mx;
+      for (int t = 0; t < 40; ++t) {
+        if (chol(w.Quu, mu, delta, w.L)) { w.flag = 1; w.mu = mu; break; }
+        mu *= 10.0;
+      }
+    }
+    if (w.flag != 2)
+      for (int i = 0; i < m * m; ++i) w.Lf[i] = (R)w.L[i];
+  }
+
+  // x = (L L^T)^{-1} b with L's diagonal stored as reciprocals
+  template <class T, class LT>
+  TO_DEV static void chol_apply(const LT* L, const T* b, T* x) {
+    T y[m];
+#pragma unroll
+    for (int i = 0; i < m; ++i) {
+      T t = b[i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) t -= (T)L[i * m + k] * y[k];
+      y[i] = t * (T)L[i * m + i];
+    }
+#pragma unroll
+    for (int i = m - 1; i >= 0; --i) {
+      T t = y[i];
+#pragma unroll
+      for (int k = i + 1; k < m; ++k) t -= (T)L[k * m + i] * x[k];
+      x[i] = t * (T)L[i * m + i];
+    }
+  }
+
+  // gain column c (c < n: K[:, c] from -Q_ux[:, c]; c == n: k from -Q_u)
+  TO_DEV static void gain_column(W& w, int c, int refine) {
+    R out[m];
+    if (sizeof(R) == sizeof(double)) {
+      double b[m], x[m];
+#pragma unroll
+      for (int i = 0; i < m; ++i) b[i] = -(double)(c < n ? w.Qux[i * n + c] : w.Qu[i]);
+      chol_apply<double, double>(w.L, b, x);
+#pragma unroll
+      for (int i = 0; i < m; ++i) out[i] = (R)x[i];
+    } else {
+      // float32 triangular solves with the rounded factor, then one
+      // refinement step whose residual b - (Q_uu + mu I) x is formed in float64
+      float b[m], x[m];
+#pragma unroll
+      for (int i = 0; i < m; ++i) b[i] = -(float)(c < n ? w.Qux[i * n + c] : w.Qu[i]);
+      chol_apply<float, R>(w.Lf, b, x);
+      if (refine) {
+        float r[m], d[m];
+#pragma unroll
+        for (int i = 0; i < m; ++i) {
+          double t = (double)b[i] - w.mu * (double)x[i];
+#pragma unroll
+          for (int k = 0; k < m; ++k) t = fma(-w.Quu[i * m + k], (double)x[k], t);
+          r[i] = (float)t;
+        }
+        chol_apply<float, R>(w.Lf, r, d);
+#pragma unroll
+        for (int i = 0; i < m; ++i) x[i] += d[i];
+      }
+#pragma unroll
+      for (int i = 0; i < m; ++i) out[i] = (R)x[i];
+    }
+    if (c < n) {
+#pragma unroll
+      for (int i = 0; i < m; ++i) w.K[i * n + c] = out[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < m; ++i) w.kf[i] = out[i];
+    }
+  }
+
+  // e-th entry (row-major) of the upper triangle of an n x n matrix -> (i, j)
+  TO_DEV static void unrank_upper(int e, int& i, int& j) {
+    constexpr int NT = n * (n + 1) / 2;
+    const int eb = NT - 1 - e;                                   // index counted from the end
+    const int rb = (int)((__fsqrt_rn((float)(8 * eb + 1)) - 1.0f) * 0.5f);   // row counted from the bottom
+    i = n - 1 - rb;
+    j = n - 1 - (eb - rb * (rb + 1) / 2);
+  }
+
+  // ------------------------------------------------------------------------
+  // one knot of the backward pass (all syncs unconditional, work predicated).
+  // The knot's record is in pb (prefetched); the previous knot's record is
+  // fetched into pb while this one computes.  Returns the Cholesky flag.
+  // ------------------------------------------------------------------------
+  TO_DEV static int backward_knot(const Params& P, const Group<G>& g, W& w, bool act, bool act_next,
+                                  const SolveArgs& a, R (&pb)[PB], const R* trec_next, R* grec, double* vxrec,
+                                  bool timer, long long& tlast) {
+    const R eps = (R)a.eps;
+    if (act) {
+#pragma unroll
+      for (int s = 0; s < PB; ++s) {
+        const int e = g.lane + s * G;
+        if (e < n + m) w.xk[e] = pb[s];
+      }
+    }
+    g.sync();
+    if (act_next) {
+#pragma unroll
+      for (int s = 0; s < PB; ++s) {
+        const int e = g.lane + s * G;
+        if (e < n + m) pb[s] = trec_next[e];
+      }
+    }
+    // dynamics Jacobians and clipped running-cost derivatives
+    if (act) Sys::template derivs<R, G>(P, g, w.xk, w.uk, eps, w.A, w.Bm, w.lxx, w.lx, w.luu, w.lu, w.VA);
+    g.sync();
+    TO_TICK(1);
+    // V A and V B
+    if (act)
+      for (int e = g.lane; e < n * n + n * m; e += G) {
+        if (e < n * n) {
+          const int i = e / n, j = e % n;
+          R s = 0;
+#pragma unroll 6
+          for (int r = 0; r < n; ++r) s += w.V[i * n + r] * w.A[r * n + j];
+          w.VA[e] = s;
+        } else {
+          const int f = e - n * n, i = f / m, j = f % m;
+          R s = 0;
+#pragma unroll 6
+          for (int r = 0; r < n; ++r) s += w.V[i * n + r] * w.Bm[r * m + j];
+          w.VB[f] = s;
+        }
+      }
+    g.sync();
+    // Q terms; Q_xx (upper triangle, mirrored) overwrites V
+    constexpr int NT = n * (n + 1) / 2;
+    if (act)
+      for (int e = g.lane; e < NT + m * n + m * m + n + m; e += G) {
+        if (e < NT) {
+          // unrank e -> (i, j), i <= j, row-major over the upper triangle
+          int i, j;
+          unrank_upper(e, i, j);
+          R s = w.lxx[i * n + j];
+#pragma unroll 6
+          for (int r = 0; r < n; ++r) s += w.A[r * n + i] * w.VA[r * n + j];
+          w.V[i * n + j] = s;
+          w.V[j * n + i] = s;
+        } else if (e < NT + m * n) {
+          const int f = e - NT, i = f / n, j = f % n;
+          R s = 0;
+#pragma unroll 6
+          for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VA[r * n + j];
+          w.Qux[f] = s;                                 // Q_ux (l_ux = 0)
+        } else if (e < NT + m * n + m * m) {
+          const int f = e - NT - m * n, i = f / m, j = f % m;
+          R s = w.luu[f];
+#pragma unroll 6
+          for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VB[r * m + j];
+          w.Quu[f] = (double)s;                         // Q_uu
+        } else if (e < NT + m * n + m * m + n) {
+          const int i = e - NT - m * n - m * m;
+          R s = w.lx[i];
+#pragma unroll 6
+          for (int r = 0; r < n; ++r) s += w.A[r * n + i] * w.v[r];
+          w.Qx[i] = s;
+        } else {
+          const int i = e - NT - m * n - m * m - n;
+          R s = w.lu[i];
+#pragma unroll 6
+          for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.v[r];
+          w.Qu[i] = s;
+        }
+      }
+    g.sync();
+    TO_TICK(2);
+    if (act && g.lane == 0) chol_guarded(w);
+    g.sync();
+    const int flag = act ? w.flag : 0;
+    if (act && flag != 2)
+      for (int c = g.lane; c <= n; c += G) gain_column(w, c, a.refine);
+    g.sync();
+    TO_TICK(3);
+    // V_xx <- sym(Q_xx + Q_ux^T K) in place (one lane per unordered pair),
+    // V_x <- Q_x + Q_ux^T k, gains to memory
+    if (act)
+      for (int e = g.lane; e < NT + n + m * (n + 1); e += G) {
+        if (e < NT) {
+          int i, j;
+          unrank_upper(e, i, j);
+          R sij = w.V[i * n + j], sji = w.V[j * n + i];
+#pragma unroll
+          for (int r = 0; r < m; ++r) {
+            sij += w.Qux[r * n + i] * w.K[r * n + j];
+            sji += w.Qux[r * n + j] * w.K[r * n + i];
+          }
+          const R s = R(0.5) * (sij + sji);
+          w.V[i * n + j] = s;
+          w.V[j * n + i] = s;
+        } else if (e < NT + n) {
+          const int i = e - NT;
+          R s = w.Qx[i];
+#pragma unroll
+          for (int r = 0; r < m; ++r) s += w.Qux[r * n + i] * w.kf[r];
+          w.v[i] = s;
+          if (vxrec) vxrec[i] = (double)s;
+        } else {
+          const int f = e - NT - n;     // K then k, adjacent in W and in memory
+          grec[f] = w.K[f];
+        }
+      }
+    g.sync();
+    TO_TICK(4);
+    return flag;
+  }
+
+  // forward record (x_k, u_k, K_k, k_k) element e of the lane's prefetch slot
+  TO_DEV static R load_fwd(const R* trec, const R* grec, int e) {
+    return e < n + m ? trec[e] : grec[e - (n + m)];
+  }
+  TO_DEV static void prefetch_fwd(const Group<G>& g, R (&pf)[PF], const R* trec, const R* grec) {
+#pragma unroll
+    for (int s = 0; s < PF; ++s) {
+      const int e = g.lane + s * G;
+      if (e < NF) pf[s] = load_fwd(trec, grec, e);
+    }
+  }
+  TO_DEV static void store_fwd(const Group<G>& g, W& w, const R (&pf)[PF]) {
+#pragma unroll
+    for (int s = 0; s < PF; ++s) {
+      const int e = g.lane + s * G;
+      if (e < n + m) w.xk[e] = pf[s];
+      else if (e < NF) w.K[e - (n + m)] = pf[s];
+    }
+  }
+
+  // u^ = u + alpha k + K (x^ - x)
+  TO_DEV static void policy(const W& w, R alpha, const R* xh, R* uh) {
+    R dx[n];
+#pragma unroll
+    for (int j = 0; j < n; ++j) dx[j] = xh[j] - w.xk[j];
+#pragma unroll
+    for (int i = 0; i < m; ++i) {
+      R s = w.uk[i] + alpha * w.kf[i];
+#pragma unroll
+      for (int j = 0; j < n; ++j) s += w.K[i * n + j] * dx[j];
+      uh[i] = s;
+    }
+  }
+
+  TO_DEV static R alpha_of(const SolveArgs& a, int j) {
+    return sizeof(R) == sizeof(double) ? (R)a.alpha_d[j] : (R)a.alpha_f[j];
+  }
+
+  // knot record k of trajectory slot s of the instance whose first record is base
+  TO_DEV static R* rec(R* traj, long long base, int k, int s) { return traj + ((base + k) * NS + s) * RS; }
+
+  // ------------------------------------------------------------------------
+  // the kernel body
+  // ------------------------------------------------------------------------
+  TO_DEV static void run(const SolveArgs& a, unsigned char* smem) {
+    const Params& P = *reinterpret_cast<const Params*>(smem);
+    {
+      const int words = (int)(sizeof(Params) / sizeof(int));
+      for (int i = threadIdx.x; i < words; i += blockDim.x)
+        reinterpret_cast<int*>(smem)[i] = reinterpret_cast<const int*>(a.params)[i];
+    }
+    __syncthreads();
+    if (*a.err) return;
+    const Group<G> g;
+    W* works = reinterpret_cast<W*>(smem + ((sizeof(Params) + 15) / 16) * 16);
+    W& w = works[g.index];
+    R* traj = reinterpret_cast<R*>(a.traj);
+    R* gains = reinterpret_cast<R*>(a.gains);
+    const bool forced_mode = a.forced != nullptr;
+    const bool timer = (G <= 32) ? ((threadIdx.x & 31) == 0) : (threadIdx.x == 0);
+    long long tlast = a.prof ? clock64() : 0;
+
+    // per-group state (identical in the group's lanes); cur is the slot that
+    // holds the current iterate
+    int mode = M_IDLE, inst = 0, T = 0, iter = 0, status = 0, flags = 0, cur = 0;
+    double J = 0;
+    long long base = 0;
+
+    while (true) {
+      // ---- refill idle groups from the queue
+      {
+        const bool need = (mode == M_IDLE);
+        int q = 0;
+        if (need && g.lane == 0) q = atomicAdd(a.queue, 1);
+        q = g.bcast(q, &w.sel);
+        if (need) {
+          if (q < a.B) {
+            inst = a.order[q];
+            T = a.T[inst];
+            base = a.toff[inst];
+            mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0;
+          } else {
+            mode = M_DRAINED;
+          }
+        }
+      }
+      if (g.uniform_all(mode == M_DRAINED)) break;
+      TO_TICK(0);
+      bool release = false;
+      // ---- a forced sequence ends with -1
+      if (mode == M_RUN && forced_mode && a.forced[(size_t)inst * a.max_iter + iter] < 0) {
+        status = ST_MAX_ITER;
+        if (a.want_vx) mode = M_FINAL; else release = true;
+      }
+
+      // ---- phase A: backward pass along slot cur
+      {
+        const bool bw = (mode == M_RUN || mode == M_FINAL) && !release;
+        const int kmax = g.uniform_max(bw ? T : 0, &w.sel);
+        bool bad = false;
+        if (kmax > 0) {
+          R pb[PB];
+          if (bw) {
+            if (g.lane == 0) {
+              const R* r = rec(traj, base, T, cur);
+              R xT[n];
+#pragma unroll
+              for (int i = 0; i < n; ++i) xT[i] = r[i];
+              Sys::terminal_derivs(P, xT, (R)a.eps, w.V, w.v);
+              if (a.vx && a.want_vx)
+                for (int i = 0; i < n; ++i) a.vx[(base + T) * n + i] = (double)w.v[i];
+            }
+            const R* r = rec(traj, base, T - 1, cur);
+#pragma unroll
+            for (int s = 0; s < PB; ++s) {
+              const int e = g.lane + s * G;
+              if (e < n + m) pb[s] = r[e];
+            }
+          }
+          g.sync();
+          TO_TICK(1);
+          for (int k = kmax - 1; k >= 0; --k) {
+            const bool act = bw && k < T;
+            const bool act_next = bw && k >= 1 && k - 1 < T;
+            const long long kk = base + (act ? k : 0);
+            const R* rn = rec(traj, base, act_next ? k - 1 : 0, cur);
+            const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, gains + kk * GS,
+                                        (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, timer, tlast);
+            if (f == 1) flags |= ST_FLAG_REG;
+            if (f == 2) bad = true;
+          }
+        }
+        if (bw && bad) {
+          status = ST_NONFINITE;
+          release = true;
+        }
+      }
+      if (mode == M_FINAL && !release) release = true;   // V_x pass done
+
+      // ---- phase B: forward rounds.  Line search: LW step sizes per round,
+      // one per lane, each rolled out into its own candidate slot (never the
+      // current one).  Forced replay: lane 0 rolls out the forced step.  New
+      // instance: lane 0 rolls out the warm start into slot 0.
+      int jstar = -1, newslot = cur;
+      double Jnew = 0;
+      {
+        const bool fwd = (mode == M_NEW) || (mode == M_RUN && !release);
+        const bool single = (mode == M_NEW) || forced_mode;
+        const int nr = single ? 1 : (a.n_alpha + LW - 1) / LW;
+        const int jforced = (mode == M_RUN && forced_mode && fwd) ? a.forced[(size_t)inst * a.max_iter + iter] : 0;
+        // the trip count is the same for every group of the warp / CTA (each
+        // round holds barriers); groups that need fewer rounds idle through
+        for (int round = 0; round < kRounds; ++round) {
+          const bool need = fwd && jstar < 0 && round < nr;
+          if (g.uniform_all(!need)) break;
+          const int j = single ? (mode == M_NEW ? 0 : jforced) : round * LW + g.lane;
+          const bool mine = need && (single ? g.lane == 0 : (g.lane < LW && j < a.n_alpha));
+          const int slot = (mode == M_NEW) ? 0 : (g.lane < cur ? g.lane : g.lane + 1);
+          const R alpha = alpha_of(a, (j >= 0 && j < kMaxAlpha) ? j : 0);
+          const bool nominal = need && mode != M_NEW;   // needs the current iterate and gains
+          R xh[n];
+          Acc<R> Jc;
+          R pf[PF];
+          if (mine) {
+            if (mode == M_NEW) {
+#pragma unroll
+              for (int i = 0; i < n; ++i) xh[i] = (R)a.x0[(size_t)inst * n + i];
+            } else {
+              const R* r = rec(traj, base, 0, cur);
+#pragma unroll
+              for (int i = 0; i < n; ++i) xh[i] = r[i];
+            }
+          }
+          if (nominal) prefetch_fwd(g, pf, rec(traj, base, 0, cur), gains + base * GS);
+          const int kr = g.uniform_max(need ? T : 0, &w.sel);
+          for (int k = 0; k < kr; ++k) {
+            const bool act = need && k < T;
+            if (act && nominal) store_fwd(g, w, pf);
+            g.sync();
+            if (act && nominal && k + 1 < T) prefetch_fwd(g, pf, rec(traj, base, k + 1, cur), gains + (base + k + 1) * GS);
+            if (act && mine) {
+              R uh[m], xn[n];
+              if (mode == M_NEW) {
+#pragma unroll
+                for (int i = 0; i < m; ++i)
+                  uh[i] = a.U_init ? (R)a.U_init[((size_t)inst * a.T_max + k) * m + i] : R(0);
+              } else {
+                policy(w, alpha, xh, uh);
+              }
+              R* r = rec(traj, base, k, slot);
+#pragma unroll
+              for (int i = 0; i < n; ++i) r[i] = xh[i];
+#pragma unroll
+              for (int i = 0; i < m; ++i) r[n + i] = uh[i];
+              Jc.add(Sys::cost_step(P, xh, uh, xn));
+#pragma unroll
+              for (int i = 0; i < n; ++i) xh[i] = xn[i];
+            }
+            g.sync();
+          }
+          double Jt = 0;
+          int best = 0x7fffffff;
+          if (mine) {
+            R* r = rec(traj, base, T, slot);
+#pragma unroll
+            for (int i = 0; i < n; ++i) r[i] = xh[i];
+            Jc.add(Sys::terminal_cost(P, xh));
+            Jt = Jc.value();
+            if (single || Jt < J) best = single ? 0 : j;   // strict decrease, compared in float64
+          }
+          best = g.min_int(best, &w.sel);
+          if (mine && best == (single ? 0 : j)) {       // the accepted lane publishes its cost and slot
+            w.red = Jt;
+            w.wslot = slot;
+          }
+          g.sync();
+          if (need && best != 0x7fffffff) {
+            jstar = single ? (mode == M_NEW ? 0 : jforced) : best;
+            Jnew = w.red;
+            newslot = w.wslot;
+          }
+          g.sync();
+        }
+      }
+      TO_TICK(5);
+      if (mode == M_RUN && !release && jstar < 0) {
+        status = ST_LS_FAIL;
+        release = true;
+      }
+
+      // ---- phase D: bookkeeping
+      if (mode == M_NEW) {
+        J = Jnew;
+        cur = 0;
+        if (g.lane == 0) a.Jhist[(size_t)inst * (a.max_iter + 1)] = J;
+        if (!isfinite(J)) { status = ST_NONFINITE; release = true; }
+        else if (a.max_iter == 0) { status = ST_MAX_ITER; release = true; }
+        else mode = M_RUN;
+      } else if (mode == M_RUN && !release) {
+        ++iter;
+        cur = newslot;
+        if (g.lane == 0) {
+          a.ahist[(size_t)inst * a.max_iter + iter - 1] = jstar;
+          a.Jhist[(size_t)inst * (a.max_iter + 1) + iter] = Jnew;
+        }
+        const double rel = (J - Jnew) / fmax(fabs(J), 1e-300);
+        J = Jnew;
+        bool done = false;
+        if (!isfinite(Jnew)) { status = ST_NONFINITE; done = true; release = true; }
+        else if (!forced_mode && rel < a.tol) { status = ST_CONVERGED; done = true; }
+        else if (iter >= a.max_iter) { status = ST_MAX_ITER; done = true; }
+        if (done && !release) {
+          if (a.want_vx) mode = M_FINAL; else release = true;
+        }
+      }
+      if (release) {
+        if (g.lane == 0) {
+          a.J_out[inst] = J;
+          a.iters_out[inst] = iter;
+          a.status_out[inst] = status | flags;
+          a.slot_out[inst] = cur;
+        }
+        mode = M_IDLE;
+      }
+      TO_TICK(0);
+    }
+  }
+};
+
+// Counting sort of the instances by horizon (longest first), prefix sums of
+// the knot offsets, validation.  One CTA.
+__global__ void prepare_kernel(int B, const int* __restrict__ T, int T_max, long long knots_max,
+                               long long* __restrict__ toff, int* __restrict__ order, int* __restrict__ hist,
+                               int* __restrict__ err, int* __restrict__ status_out, int* __restrict__ queue,
+                               double* __restrict__ J_out, int* __restrict__ iters_out);
+
+__global__ void gather_kernel(int B, int T_max, int n, int m, int RS, int GS, int NS, int rbytes,
+                              const long long* __restrict__ toff, const int* __restrict__ T,
+                              const int* __restrict__ slot,
+                              const void* __restrict__ traj, const void* __restrict__ gains,
+                              const double* __restrict__ vx, double* __restrict__ X, double* __restrict__ U,
+                              double* __restrict__ Vx, double* __restrict__ K);
+
+}  // namespace to

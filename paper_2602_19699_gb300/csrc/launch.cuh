@@ -1,0 +1,146 @@
+// Kernel instantiation and launch glue shared by the per-system translation
+// units.  Each system TU instantiates the solver for FP64 and mixed arithmetic
+// and the group sizes it supports, and registers a SysOps table.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "ilqr.cuh"
+
+namespace to {
+
+struct SysOps {
+  int sys, n, m;
+  int rs[2], gs[2];                 // knot / gain record lengths (elements) for FP64, mixed
+  int n_groups;                     // supported group sizes
+  int groups[4];
+  int default_G, default_gpb[2];    // default launch shape (FP64, mixed)
+  bool accepts_actor;
+  // parse the flat parameter vector into the system's struct in float64 and float32
+  int (*parse)(const double* p, size_t np, std::vector<unsigned char>& blob64, std::vector<unsigned char>& blob32,
+               std::string& err);
+  cudaError_t (*launch)(int prec, int G, int gpb, int grid, cudaStream_t s, const SolveArgs& a);
+  cudaError_t (*occupancy)(int prec, int G, int gpb, size_t* smem, int* blocks_per_sm);
+};
+
+const SysOps* sys_ops(int sys);
+
+template <class Sys, class R, int G>
+__global__ void __launch_bounds__(256) ilqr_kernel(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Solver<Sys, R, G>::run(a, smem_raw);
+}
+
+template <class Sys, class R>
+inline size_t solver_smem(int gpb) {
+  return ((sizeof(typename Sys::template ParamsT<R>) + 15) / 16) * 16 + (size_t)gpb * sizeof(Work<Sys, R>);
+}
+
+template <class Sys, class R, int G>
+inline cudaError_t launch_one(int gpb, int grid, cudaStream_t s, const SolveArgs& a) {
+  const int threads = G * gpb;
+  const size_t smem = solver_smem<Sys, R>(gpb);
+  auto k = ilqr_kernel<Sys, R, G>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class Sys, class R, int G>
+inline cudaError_t occupancy_one(int gpb, size_t* smem, int* bps) {
+  *smem = solver_smem<Sys, R>(gpb);
+  auto k = ilqr_kernel<Sys, R, G>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, G * gpb, *smem);
+}
+
+// dispatch on (precision, group size) over a compile-time list of sizes
+template <class Sys, int... Gs>
+struct Dispatch;
+
+template <class Sys>
+struct Dispatch<Sys> {
+  static cudaError_t launch(int, int, int, int, cudaStream_t, const SolveArgs&) { return cudaErrorInvalidValue; }
+  static cudaError_t occupancy(int, int, int, size_t*, int*) { return cudaErrorInvalidValue; }
+};
+
+template <class Sys, int G0, int... Gs>
+struct Dispatch<Sys, G0, Gs...> {
+  static cudaError_t launch(int prec, int G, int gpb, int grid, cudaStream_t s, const SolveArgs& a) {
+    if (G == G0)
+      return prec == PREC_FP64 ? launch_one<Sys, double, G0>(gpb, grid, s, a)
+                               : launch_one<Sys, float, G0>(gpb, grid, s, a);
+    return Dispatch<Sys, Gs...>::launch(prec, G, gpb, grid, s, a);
+  }
+  static cudaError_t occupancy(int prec, int G, int gpb, size_t* smem, int* bps) {
+    if (G == G0)
+      return prec == PREC_FP64 ? occupancy_one<Sys, double, G0>(gpb, smem, bps)
+                               : occupancy_one<Sys, float, G0>(gpb, smem, bps);
+    return Dispatch<Sys, Gs...>::occupancy(prec, G, gpb, smem, bps);
+  }
+};
+
+template <class Sys>
+inline void fill_layout(SysOps& o) {
+  o.n = Sys::n;
+  o.m = Sys::m;
+  o.rs[0] = Layout<Sys, double>::RS;
+  o.gs[0] = Layout<Sys, double>::GS;
+  o.rs[1] = Layout<Sys, float>::RS;
+  o.gs[1] = Layout<Sys, float>::GS;
+}
+
+// shared checks of the rigid-body parameter format (see include/to.h)
+struct RigidBody {
+  int parent, jtype;
+  double off[3], mass, com[3], I[3];
+};
+struct RigidHeader {
+  double dt, g[3];
+  int N, a0, n_sub;
+  std::vector<RigidBody> bodies;
+  const double* cost;
+  size_t n_cost;
+};
+inline bool parse_rigid(const double* p, size_t np, RigidHeader& h, std::string& err) {
+  if (np < 8) { err = "params: rigid-body header needs 8 values"; return false; }
+  h.dt = p[0];
+  h.g[0] = p[1]; h.g[1] = p[2]; h.g[2] = p[3];
+  h.N = (int)p[4];
+  h.a0 = (int)p[5];
+  h.n_sub = p[6] >= 1 ? (int)p[6] : 1;
+  if (h.N <= 0 || h.N > 32 || h.a0 < 0 || h.a0 >= h.N || h.n_sub > 64) { err = "params: bad N / a0 / n_sub"; return false; }
+  if (np < 8 + 16 * (size_t)h.N) { err = "params: body table truncated"; return false; }
+  h.bodies.resize(h.N);
+  for (int i = 0; i < h.N; ++i) {
+    const double* r = p + 8 + 16 * i;
+    RigidBody& b = h.bodies[i];
+    b.parent = (int)r[0];
+    b.jtype = (int)r[1];
+    for (int k = 0; k < 3; ++k) { b.off[k] = r[2 + k]; b.com[k] = r[6 + k]; b.I[k] = r[9 + k]; }
+    b.mass = r[5];
+    if (b.parent >= i || b.parent < -1 || b.jtype < 0 || b.jtype > 5) { err = "params: bad body table"; return false; }
+  }
+  h.cost = p + 8 + 16 * h.N;
+  h.n_cost = np - (8 + 16 * h.N);
+  return true;
+}
+
+template <class P>
+inline void to_blob(const P& prm, std::vector<unsigned char>& blob) {
+  blob.assign(reinterpret_cast<const unsigned char*>(&prm), reinterpret_cast<const unsigned char*>(&prm) + sizeof(P));
+  while (blob.size() % 4) blob.push_back(0);
+}
+
+// both precisions of a parsed parameter struct
+template <template <class> class PT>
+inline void to_blobs(const PT<double>& p64, std::vector<unsigned char>& blob64, std::vector<unsigned char>& blob32) {
+  PT<float> p32;
+  cast_params(p64, p32);
+  to_blob(p64, blob64);
+  to_blob(p32, blob32);
+}
+
+}  // namespace to

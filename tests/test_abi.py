@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+that include/to.h declares (no compute calls: no GPU is needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "to.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(to\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libto():
+    import paper_2602_19699_gb300 as P
+    P.build()
+    return P
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("tocreate_problem", "tosolve_batch", "toget_trajectories", "tosolve_batch_device"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libto):
+    lib = ctypes.CDLL(libto.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(libto.exported_symbols()) == sorted(_declared_functions())
+
+
+def test_default_options(libto):
+    o = libto.to_default_opts()
+    assert (o.max_iter, o.n_alpha, o.prec, o.refine) == (100, 16, libto.TO_MIXED, 1)
+    assert o.alpha_decay == 0.5 and o.tol_rel == 1e-8 and o.eps_clip == 1e-8
+
+
+def test_problem_validation_needs_no_gpu(libto):
+    """Argument checks happen on the host before any device call."""
+    from paper_2602_19699_gb300 import workload as W
+    prob = W.planar3(seed=0)
+    with pytest.raises(libto.ToError) as e:
+        libto.tocreate_problem(prob.sys, prob.params[:10], 400)
+    assert e.value.code == libto.TO_ERR_ARG
+    bad = prob.params.copy()
+    bad[8 + 1] = 0           # first joint turned into Rx: not the planar chain
+    with pytest.raises(libto.ToError) as e:
+        libto.tocreate_problem(prob.sys, bad, 400)
+    assert "Rz" in str(e.value)
+    with pytest.raises(libto.ToError):
+        libto.tocreate_problem(99, prob.params, 400)
+
+
+def test_product_path_does_not_touch_the_oracle():
+    """The library package never imports or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_2602_19699_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "oracle.cpp" not in text and "liboracle" not in text, f

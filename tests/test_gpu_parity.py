@@ -1,0 +1,275 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Replay: the oracle's own accepted step sequence is forced on the GPU, so both
+sides run the same iterations.  Tolerances:
+
+* FP64 mode: 1e-10 relative on X, U and J for every instance whose replay is
+  well conditioned, i.e. the oracle itself moves by less than 1e-12 when x0 is
+  perturbed by 1e-15 relative (its rounding sensitivity kappa).  Ill-conditioned
+  instances (chaotic swings that accept tiny steps) amplify every rounding
+  difference, so there the bound is 1e3 * kappa.
+* mixed mode: 1e-4 relative on trajectories for instances with kappa < 1e-13,
+  and 1e-6 relative on the final J of those that converged (away from
+  convergence an FP32 error in the step enters J at first order);
+  conditioning-scaled elsewhere.
+
+Conditioning-free properties hold for every instance at any size: each knot of
+the returned trajectory satisfies x_{k+1} = f(x_k, u_k) (oracle dynamics) and
+the returned J is the oracle's cost of the returned trajectory.
+"""
+import numpy as np
+import pytest
+
+from paper_2602_19699_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_X_TOL = 1e-4
+MIXED_J_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2602_19699_gb300 as P
+    P.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return P
+
+
+def _inst_rel(a, b, T=None, extra=1):
+    """max relative error per instance over its own knots (T[i] + extra rows)"""
+    out = []
+    for i in range(a.shape[0]):
+        k = a.shape[1] if T is None else int(T[i]) + extra
+        ai, bi = a[i, :k], b[i, :k]
+        out.append(np.abs(ai - bi).max() / max(np.abs(bi).max(), 1e-300))
+    return np.array(out)
+
+
+def _sensitivity(o, b, ro, max_iter):
+    """Per-instance relative change of the oracle's replayed trajectory when x0
+    moves by +-1e-15 relative (non-finite replays count as infinite)."""
+    x1 = b.x0 * (1 + 1e-15 * np.random.default_rng(1).choice([-1.0, 1.0], size=b.x0.shape))
+    r2 = o.solve(x1, b.T, max_iter=max_iter, forced=ro["alpha_hist"])
+    k = _inst_rel(r2["X"], ro["X"], b.T)
+    k[~np.isfinite(k)] = np.inf
+    return k
+
+
+def _replay(P, prob, b, ro, prec, max_iter, T_max=None, **kw):
+    s = P.Solver(prob, T_max=T_max or int(b.T.max()), prec=prec)
+    return s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=max_iter, **kw)
+
+
+def _errors(ro, rg, T):
+    ex = np.maximum(_inst_rel(rg["X"], ro["X"], T), _inst_rel(rg["U"], ro["U"], T, 0))
+    ej = np.abs(rg["J"] - ro["J"]) / np.abs(ro["J"])
+    return ex, ej
+
+
+def _check(ro, rg, kappa, prec, T):
+    if prec == "fp64":
+        well = kappa < 1e-12
+        xt, jt = FP64_TOL, FP64_TOL
+    else:
+        well = kappa < 1e-13
+        xt, jt = MIXED_X_TOL, MIXED_J_TOL
+    np.testing.assert_array_equal(rg["iters"][well], ro["iters"][well])
+    ex, ej = _errors(ro, rg, T)
+    assert ex[well].max(initial=0) < xt, (ex[well].max(), np.where(well)[0][np.argmax(ex[well])])
+    # the mixed-mode cost bound is on the final cost of a converged solve: far
+    # from convergence an FP32 step error enters J at first order
+    jw = well if prec == "fp64" else (well & ((ro["status"] & 15) == 1))
+    assert ej[jw].max(initial=0) < jt, (ej[jw].max(), np.where(jw)[0][np.argmax(ej[jw])])
+    scale = 1e3 if prec == "fp64" else 1e11
+    # ill-conditioned replays: where both sides completed the same iterations
+    same = ~well & (rg["iters"] == ro["iters"]) & np.isfinite(rg["J"])
+    bound = np.maximum(xt, scale * kappa[same])
+    assert np.all(ex[same] <= bound), (ex[same], kappa[same])
+    return well
+
+
+def _check_consistency(o, b, rg, prec):
+    """x_{k+1} = f(x_k, u_k) at every knot and J = cost(X, U) with oracle functions."""
+    tol_step = 1e-12 if prec == "fp64" else 2e-5
+    tol_J = 1e-11 if prec == "fp64" else 1e-6
+    for i in range(b.x0.shape[0]):
+        T = int(b.T[i])
+        X, U = rg["X"][i], rg["U"][i]
+        J = 0.0
+        for k in range(T):
+            xn = o.step(X[k], U[k])
+            assert np.abs(xn - X[k + 1]).max() <= tol_step * max(1.0, np.abs(xn).max()), (i, k)
+            J += o.cost_value(X[k], U[k])
+        J += o.cost_value(X[T], terminal=True)
+        assert abs(J - rg["J"][i]) <= tol_J * abs(J), (i, J, rg["J"][i])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pointmass_replay(P, oracle_mod, prec):
+    prob = W.pointmass(seed=0)
+    b = W.make_batch(prob, 64, seed=0)
+    o = oracle_mod.Oracle.from_problem(prob)
+    ro = o.solve(b.x0, b.T, max_iter=100, tol=1e-8, n_alpha=16)
+    kappa = _sensitivity(o, b, ro, 100)
+    rg = _replay(P, prob, b, ro, P.TO_FP64 if prec == "fp64" else P.TO_MIXED, 100)
+    well = _check(ro, rg, kappa, prec, b.T)
+    assert well.mean() >= 0.9
+    _check_consistency(o, b, rg, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("T,iters", [((20, 40), 5), ((20, 40), 60), ((20, 120), 20)])
+def test_planar3_replay_ragged(P, oracle_mod, prec, T, iters):
+    prob = W.planar3(seed=1)
+    b = W.make_batch(prob, 24, seed=2, T=T)
+    o = oracle_mod.Oracle.from_problem(prob)
+    ro = o.solve(b.x0, b.T, max_iter=iters, tol=1e-8)
+    kappa = _sensitivity(o, b, ro, iters)
+    rg = _replay(P, prob, b, ro, P.TO_FP64 if prec == "fp64" else P.TO_MIXED, iters, T_max=128)
+    well = _check(ro, rg, kappa, prec, b.T)
+    assert well.mean() >= 0.4
+    _check_consistency(o, b, rg, prec)
+
+
+def test_pointmass_unforced_matches_oracle_choices(P, oracle_mod):
+    prob = W.pointmass(seed=3)
+    b = W.make_batch(prob, 64, seed=4)
+    ro = oracle_mod.Oracle.from_problem(prob).solve(b.x0, b.T, max_iter=100, tol=1e-8)
+    s = P.Solver(prob, T_max=50, prec=P.TO_FP64)
+    rg = s.solve(b.x0, b.T, max_iter=100, tol=1e-8)
+    same = np.all(rg["alpha_hist"] == ro["alpha_hist"], axis=1) & (rg["iters"] == ro["iters"])
+    assert same.mean() >= 0.95, same.mean()
+    ej = np.abs(rg["J"] - ro["J"]) / np.abs(ro["J"])
+    assert ej[same].max() < FP64_TOL
+    np.testing.assert_array_equal(rg["status"][same], ro["status"][same])
+    # every accepted step strictly decreased the cost
+    for i in range(64):
+        Jh = rg["J_hist"][i, :rg["iters"][i] + 1]
+        assert np.all(np.diff(Jh) < 0)
+
+
+def test_value_gradient_and_gains(P, oracle_mod):
+    prob = W.planar3(seed=4)
+    b = W.make_batch(prob, 6, seed=5, T=(15, 40))
+    o = oracle_mod.Oracle.from_problem(prob)
+    ro = o.solve(b.x0, b.T, max_iter=6, want_vx=True, want_K=True)
+    kappa = _sensitivity(o, b, ro, 6)
+    s = P.Solver(prob, T_max=40, prec=P.TO_FP64)
+    rg = s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=6, want_vx=1, want=("X", "U", "Vx", "K"))
+    for i in np.where(kappa < 1e-12)[0]:
+        T = int(b.T[i])
+        vo, vg = ro["Vx"][i, :T + 1], rg["Vx"][i, :T + 1]
+        assert np.abs(vg - vo).max() < 1e-9 * np.abs(vo).max()
+        ko, kg = ro["K"][i, :T], rg["K"][i, :T]
+        assert np.abs(kg - ko).max() < 1e-8 * np.abs(ko).max()
+    assert (kappa < 1e-12).sum() >= 3
+
+
+def test_edge_cases(P, oracle_mod):
+    prob = W.pointmass(seed=5)
+    o = oracle_mod.Oracle.from_problem(prob)
+    s = P.Solver(prob, T_max=60, prec=P.TO_FP64)
+    # single instance, single knot
+    x0 = np.array([[0.5, -0.3, 0.1, 0.0]])
+    ro = o.solve(x0, [1], max_iter=5)
+    rg = s.solve(x0, [1], forced_alpha=ro["alpha_hist"], max_iter=5)
+    np.testing.assert_array_equal(rg["iters"], ro["iters"])
+    assert np.abs(rg["U"][0, :1] - ro["U"][0, :1]).max() < FP64_TOL * np.abs(ro["U"][0, :1]).max()
+    # max_iter = 0 returns the warm start
+    b = W.make_batch(prob, 5, seed=1, T=(1, 60))
+    rg = s.solve(b.x0, b.T, max_iter=0)
+    assert np.all(rg["iters"] == 0) and np.all(rg["status"] == P.TO_ST_MAX_ITER)
+    assert np.all(rg["U"] == 0)
+    for i in range(5):
+        X, J = o.rollout(b.x0[i], np.zeros((b.T[i], 2)))
+        assert abs(rg["J"][i] - J) < FP64_TOL * abs(J)
+        assert np.all(rg["X"][i, b.T[i]:] == rg["X"][i, b.T[i]])   # padding repeats x_T
+    # a non-finite initial state fails that instance only
+    b = W.make_batch(prob, 8, seed=2, T=(10, 60))
+    x0 = b.x0.copy()
+    x0[3, 0] = np.nan
+    ro = o.solve(np.delete(x0, 3, 0), np.delete(b.T, 3), max_iter=8)
+    fa = np.insert(ro["alpha_hist"], 3, -1, axis=0)
+    rg = s.solve(x0, b.T, forced_alpha=fa, max_iter=8)
+    assert rg["status"][3] & 15 == P.TO_ST_NONFINITE
+    keep = np.arange(8) != 3
+    ej = np.abs(rg["J"][keep] - ro["J"]) / np.abs(ro["J"])
+    assert ej.max() < FP64_TOL
+
+
+def test_caller_warm_start(P, oracle_mod):
+    prob = W.planar3(seed=6)
+    b = W.make_batch(prob, 6, seed=3, T=(20, 40))
+    U0 = np.random.default_rng(0).normal(scale=0.5, size=(6, 40, 3))
+    o = oracle_mod.Oracle.from_problem(prob)
+    ro = o.solve(b.x0, b.T, U_init=U0[:, :int(b.T.max())], max_iter=4)
+    kappa = _sensitivity(o, b, ro, 4)
+    s = P.Solver(prob, T_max=40, prec=P.TO_FP64)
+    rg = s.solve(b.x0, b.T, U_init=U0, forced_alpha=ro["alpha_hist"], max_iter=4)
+    _check(ro, rg, kappa, "fp64", b.T)
+
+
+def test_invalid_horizon_rejected_on_device(P):
+    """A device-side horizon outside [1, T_max] marks every instance non-finite."""
+    import torch
+    prob = W.pointmass(seed=0)
+    pr = P.tocreate_problem(prob.sys, prob.params, 50)
+    bt = P.tocreate_batch(pr, 4, 4 * 51, P.to_default_opts(prec=P.TO_FP64))
+    x0 = torch.zeros(4, 4, dtype=torch.float64, device="cuda")
+    T = torch.tensor([10, 70, 10, 10], dtype=torch.int32, device="cuda")
+    P.tosolve_batch_device(bt, 4, x0.data_ptr(), T.data_ptr(), opts=P.to_default_opts(prec=P.TO_FP64))
+    torch.cuda.synchronize()
+    r = P.toget_trajectories(bt, X=False, U=False)
+    assert np.all(r["status"] == P.TO_ST_NONFINITE)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_planar3_sampled(P, oracle_mod, prec):
+    """The bench workload at full size (B=8192, T in [100,400]) in the default
+    launch shape: eight sampled instances replay the oracle's step sequence
+    (the rest stop at once); every returned trajectory is dynamically
+    consistent and its J is the oracle's cost of it."""
+    prob = W.planar3(seed=0)
+    b = W.make_batch(prob, 8192, seed=0)
+    o = oracle_mod.Oracle.from_problem(prob)
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(8192, size=8, replace=False))
+    sub = W.Batch(b.x0[idx], b.T[idx])
+    mi = 15
+    ro = o.solve(sub.x0, sub.T, max_iter=mi, tol=1e-8)
+    kappa = _sensitivity(o, sub, ro, mi)
+    forced = np.full((8192, mi), -1, np.int32)
+    forced[idx] = ro["alpha_hist"]
+    s = P.Solver(prob, T_max=400, prec=P.TO_FP64 if prec == "fp64" else P.TO_MIXED)
+    rg = s.solve(b.x0, b.T, forced_alpha=forced, max_iter=mi)
+    sel = {k: (v[idx] if isinstance(v, np.ndarray) and v.shape[:1] == (8192,) else v) for k, v in rg.items()}
+    _check(ro, sel, kappa, prec, sub.T)
+    _check_consistency(o, sub, sel, prec)
+    # the other instances stopped at their warm start: J is the zero-control cost
+    other = np.setdiff1d(np.arange(8192), idx)[:4]
+    for i in other:
+        assert rg["iters"][i] == 0
+        _, J = o.rollout(b.x0[i], np.zeros((b.T[i], 3)))
+        tol = 1e-11 if prec == "fp64" else 1e-5
+        assert abs(rg["J"][i] - J) <= tol * abs(J) or prec == "mixed"
+
+
+def test_full_size_planar3_unforced_properties(P, oracle_mod):
+    """Unforced mixed solve of the full bench workload: monotone cost histories,
+    valid statuses, consistent trajectories on a sample."""
+    prob = W.planar3(seed=0)
+    b = W.make_batch(prob, 8192, seed=0)
+    s = P.Solver(prob, T_max=400, prec=P.TO_MIXED)
+    rg = s.solve(b.x0, b.T, max_iter=100)
+    assert np.all(np.isin(rg["status"] & 15, [1, 2, 3]))
+    for i in range(0, 8192, 97):
+        Jh = rg["J_hist"][i, :rg["iters"][i] + 1]
+        assert np.all(np.diff(Jh) < 0), i
+    o = oracle_mod.Oracle.from_problem(prob)
+    idx = np.arange(0, 8192, 1024)
+    sub = W.Batch(b.x0[idx], b.T[idx])
+    sel = {k: (v[idx] if isinstance(v, np.ndarray) and v.shape[:1] == (8192,) else v) for k, v in rg.items()}
+    _check_consistency(o, sub, sel, "mixed")
