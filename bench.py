@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Benchmark of the batched iLQR solver on one GB300 (or N, one process each).
+
+Workload (the paper's manipulator, synthetic): planar 3-link arm, B = 8192
+instances per GPU, horizons T ~ U{100..400}, zero-control warm start, iLQR
+with at most 100 iterations, relative-decrease tolerance 1e-8, 16 step sizes
+alpha_j = 0.5^j.  One step = one full batched solve (all iterations of every
+instance) in mixed precision.
+
+value: solves per second whose final cost is at most 1e-6 relative above the
+FP64 CPU oracle's final cost on the same instance (the fraction is measured on
+a bounded random sample that the oracle solves on the host cores; the same run
+is the CPU baseline).  Inputs are resident in HBM when the timed region starts.
+e2e: the same metric through tosolve_batch with host buffers, including the
+host->device copy of (x0, T) and the device->host copy of (X, U, J, iters,
+status) every step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "OCP solves/s at 1e-6 cost tol, batched vs plain (1 GB300); serve p50/p99 ms"
+UNIT = "solves/s"
+B_PER_GPU = 8192
+T_RANGE = (100, 400)
+MAX_ITER = 100
+TOL = 1e-8
+N_ALPHA = 16
+COST_TOL = 1e-6
+CPU_SAMPLE = 64
+PLAIN_SAMPLE = 6
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain and FP64 comparison legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(rank: int):
+    from paper_2602_19699_gb300 import workload as W
+    prob = W.planar3(seed=0)
+    batch = W.make_batch(prob, B_PER_GPU, seed=1000 + rank, T=T_RANGE)
+    return prob, batch
+
+
+# --------------------------------------------------------------------------
+# clocks sampled while the timed region runs
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = np.array([r[0] for r in rows])
+        mx = max(r[1] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower().startswith("active")})
+        load = sm[sm >= 0.5 * np.median(sm)]
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded random sample (host cores)
+# --------------------------------------------------------------------------
+def cpu_baseline_leg(prob, batch, idx, threads=0):
+    import oracle
+    o = oracle.Oracle.from_problem(prob)
+    cores = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = o.solve(batch.x0[idx], batch.T[idx], max_iter=MAX_ITER, tol=TOL, n_alpha=N_ALPHA, threads=cores)
+    dt = time.perf_counter() - t0
+    return r, dt, min(cores, len(idx))
+
+
+def solved_fraction(J, J_ref):
+    """An instance counts as solved at the cost tolerance when its final cost
+    is at most (1 + tol) times the FP64 oracle's (a lower cost is a better
+    solution of the same problem)."""
+    return float(np.mean(np.asarray(J) <= (1 + COST_TOL) * np.asarray(J_ref)))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, sms: int) -> float:
+    """152 SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def kernel_sources_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_19699_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per solver launch from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ilqr_planar3_B8192_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_sources_sha256_16") != kernel_sources_digest():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+# the GB300 arm
+# --------------------------------------------------------------------------
+def run_gb300(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_2602_19699_gb300 as P
+    from paper_2602_19699_gb300 import flops
+    P.build()
+
+    prob, b = workload(rank)
+    B = b.x0.shape[0]
+    T_MAX = T_RANGE[1]
+    knots = int(np.sum(b.T + 1))
+    problem = P.tocreate_problem(prob.sys, prob.params, T_MAX)
+    opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=MAX_ITER, tol_rel=TOL, n_alpha=N_ALPHA)
+    batch = P.tocreate_batch(problem, B, knots, opts)
+    dev = torch.device("cuda", local)
+    d_x0 = torch.tensor(b.x0, dtype=torch.float64, device=dev)
+    d_T = torch.tensor(b.T, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def solve_device():
+        P.tosolve_batch_device(batch, B, d_x0.data_ptr(), d_T.data_ptr(), opts=opts, stream=sptr)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        solve_device()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs; L2 flushed between steps
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    t_steps = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solve_device()
+        e1.record(stream)
+        e1.synchronize()
+        t_steps.append(e0.elapsed_time(e1) / 1e3)
+    barrier()
+    clk = clocks.stop()
+    launches = P.tolast_launch_count(batch) * args.steps
+    t_local = float(np.sum(t_steps))
+    t_max = t_local
+    if ws > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    # results of the last timed step
+    J_g = P.toget_trajectories(batch, X=False, U=False)
+    ah, _ = P.toget_history(batch)
+    alg = flops.solve_flops(prob.sys, prob.n, prob.m, b.T, J_g["iters"], J_g["status"], ah,
+                            lanes_per_round=8, n_alpha=N_ALPHA, refine=True)
+
+    # ---- e2e: host buffers through the public API, copies inside the region
+    pin_x0 = torch.tensor(b.x0, dtype=torch.float64).pin_memory().numpy()
+    pin_T = torch.tensor(b.T, dtype=torch.int32).pin_memory().numpy()
+    out_X = torch.empty((B, T_MAX + 1, prob.n), dtype=torch.float64).pin_memory().numpy()
+    out_U = torch.empty((B, T_MAX, prob.m), dtype=torch.float64).pin_memory().numpy()
+    out_J = torch.empty(B, dtype=torch.float64).pin_memory().numpy()
+    out_it = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
+    out_st = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
+    def solve_e2e():
+        P.tosolve_batch(problem, pin_x0, pin_T, opts=opts, stream=sptr, batch=batch)
+        rc = P.lib().toget_trajectories(batch.handle, P._ptr(out_X), P._ptr(out_U), P._ptr(out_J), P._ptr(out_it),
+                                        P._ptr(out_st), None, None)
+        if rc != 0:
+            raise RuntimeError(P.tolast_error())
+
+    solve_e2e()
+    barrier()
+    e2e_steps = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        solve_e2e()
+        e2e_steps.append(time.perf_counter() - ts)
+    e2e_local = float(np.sum(e2e_steps))
+    e2e_max = e2e_local
+    if ws > 1:
+        tt = torch.tensor([e2e_local], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_max = float(tt.item())
+    h2d = b.x0.nbytes + b.T.astype(np.int32).nbytes
+    d2h = out_X.nbytes + out_U.nbytes + out_J.nbytes + out_it.nbytes + out_st.nbytes
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- accuracy + CPU baseline on a bounded sample (rank 0)
+    rng = np.random.default_rng(12345)
+    idx = np.sort(rng.choice(B, size=CPU_SAMPLE, replace=False))
+    ro, t_cpu, cores = cpu_baseline_leg(prob, b, idx)
+    frac_mixed = solved_fraction(J_g["J"][idx], ro["J"])
+    two_sided = float(np.mean(np.abs(J_g["J"][idx] - ro["J"]) <= COST_TOL * np.abs(ro["J"])))
+    # the oracle against itself with x0 moved by 1e-15 relative: the ceiling
+    # any re-implementation can reach on this (chaotic) workload
+    import oracle
+    x_pert = b.x0[idx] * (1 + 1e-15 * rng.choice([-1.0, 1.0], size=b.x0[idx].shape))
+    r_self = oracle.Oracle.from_problem(prob).solve(x_pert, b.T[idx], max_iter=MAX_ITER, tol=TOL, n_alpha=N_ALPHA,
+                                                    threads=cores)
+    self_one = solved_fraction(r_self["J"], ro["J"])
+    self_two = float(np.mean(np.abs(r_self["J"] - ro["J"]) <= COST_TOL * np.abs(ro["J"])))
+
+    extras = {}
+    if not args.no_extras:
+        # batched FP64 (same workload, one timed solve) and the plain
+        # one-instance-per-launch FP64 solver on a sample
+        opts64 = P.to_default_opts(prec=P.TO_FP64, max_iter=MAX_ITER, tol_rel=TOL, n_alpha=N_ALPHA)
+        b64 = P.tocreate_batch(problem, B, knots, opts64)
+        P.tosolve_batch_device(b64, B, d_x0.data_ptr(), d_T.data_ptr(), opts=opts64, stream=sptr)
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.tosolve_batch_device(b64, B, d_x0.data_ptr(), d_T.data_ptr(), opts=opts64, stream=sptr)
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        b64.B, b64.max_iter = B, MAX_ITER
+        J64 = P.toget_trajectories(b64, X=False, U=False)["J"]
+        frac64 = solved_fraction(J64[idx], ro["J"])
+        extras["batched_fp64"] = {"value": B * frac64 / t64, "raw_solves_per_s": B / t64, "ms_per_step": t64 * 1e3,
+                                  "within_tol": frac64}
+        bp = P.tocreate_batch(problem, 1, T_MAX + 1, opts64)
+        pidx = idx[:PLAIN_SAMPLE]
+        Jp = np.empty(len(pidx))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in pidx:
+            P.tosolve_batch_device(bp, 1, d_x0[i:i + 1].data_ptr(), d_T[i:i + 1].data_ptr(), opts=opts64, stream=sptr)
+        e1.record(stream)
+        e1.synchronize()
+        tp = e0.elapsed_time(e1) / 1e3
+        bp.B, bp.max_iter = 1, MAX_ITER
+        # per-instance J of the plain solver (re-run outside the timed region)
+        for k, i in enumerate(pidx):
+            P.tosolve_batch_device(bp, 1, d_x0[i:i + 1].data_ptr(), d_T[i:i + 1].data_ptr(), opts=opts64, stream=sptr)
+            Jp[k] = P.toget_trajectories(bp, X=False, U=False)["J"][0]
+        fracp = solved_fraction(Jp, ro["J"][:PLAIN_SAMPLE])
+        extras["plain_fp64_one_instance_per_launch"] = {
+            "value": len(pidx) * fracp / tp, "raw_solves_per_s": len(pidx) / tp, "sample": len(pidx),
+            "within_tol": fracp}
+
+    pk, pk_src = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    peak32 = fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0), sms)
+    achieved = alg / (t_local / args.steps) / 1e12
+    traffic = measured_traffic()
+    n = ws
+    t_step = t_max / args.steps
+    value = n * B * frac_mixed / t_step
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": n,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "precision": "mixed: f32 rollouts/derivatives/Riccati products; f64 Q_uu Cholesky, pivot test, "
+                     "refinement residual, cost comparison",
+        "data": "synthetic (seeded generator)",
+        "config": {
+            "workload": f"planar3 arm, B={B} per GPU, T~U{{{T_RANGE[0]}..{T_RANGE[1]}}}, zero warm start, "
+                        f"max_iter={MAX_ITER}, tol={TOL}, {N_ALPHA} step sizes",
+            "batch_per_gpu": B, "knots_per_gpu": knots, "parallelism": f"independent instances x{n}",
+            "l2": "flushed between steps (512 MB write); working set ~1.7 GB > L2",
+            "launch": "persistent kernel, 8 lanes per instance, 8 instances per CTA",
+        },
+        "raw_solves_per_s": n * B / t_step,
+        "within_tol": {"cost_tol": COST_TOL, "sample": int(len(idx)), "fraction": frac_mixed,
+                       "rule": "final J <= (1 + 1e-6) * J of the FP64 CPU oracle on the same instance",
+                       "two_sided_fraction": two_sided,
+                       "oracle_self_reproducibility": {"one_sided": self_one, "two_sided": self_two,
+                                                       "perturbation": "x0 * (1 +- 1e-15)"}},
+        "e2e": {"value": n * B * frac_mixed / (e2e_max / args.steps), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
+                     "frac": achieved / peak32, "traffic": traffic,
+                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                                    f"(max SM clock from {pk_src} peaks)",
+                     "algorithmic_flops_per_launch": alg},
+        "cpu_baseline": {"value": len(idx) / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(idx)} random instances of the same workload, FP64 C++ oracle, "
+                                   f"one instance per thread"},
+        "clocks": clk,
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# the reference arm: the FP64 oracle itself on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    prob, b = workload(0)
+    rng = np.random.default_rng(777)
+    per_step = 32
+    t = 0.0
+    cores = os.cpu_count() or 1
+    for s in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(b.x0.shape[0], size=per_step, replace=False))
+        _, dt, used = cpu_baseline_leg(prob, b, idx, threads=cores)
+        if s >= args.warmup:
+            t += dt
+    value = per_step * args.steps / t
+    sample = f"{per_step} random instances per step of the same workload, FP64 C++ oracle, one instance per thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"planar3 arm, T~U{{{T_RANGE[0]}..{T_RANGE[1]}}}, max_iter={MAX_ITER}, tol={TOL}",
+                   "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(cores, per_step), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

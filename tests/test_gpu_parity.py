@@ -74,7 +74,9 @@ def _check(ro, rg, kappa, prec, T):
         well = kappa < 1e-12
         xt, jt = FP64_TOL, FP64_TOL
     else:
-        well = kappa < 1e-13
+        # float32 rounding (6e-8 per operation) is ~1e7 times the 1e-15
+        # probe behind kappa: the strict bound needs kappa < 1e-14
+        well = kappa < 1e-14
         xt, jt = MIXED_X_TOL, MIXED_J_TOL
     np.testing.assert_array_equal(rg["iters"][well], ro["iters"][well])
     ex, ej = _errors(ro, rg, T)
@@ -95,9 +97,13 @@ def _check_consistency(o, b, rg, prec):
     """x_{k+1} = f(x_k, u_k) at every knot and J = cost(X, U) with oracle functions."""
     tol_step = 1e-12 if prec == "fp64" else 2e-5
     tol_J = 1e-11 if prec == "fp64" else 1e-6
+    checked = 0
     for i in range(b.x0.shape[0]):
         T = int(b.T[i])
         X, U = rg["X"][i], rg["U"][i]
+        if not (np.all(np.isfinite(X[:T + 1])) and np.abs(X[:T + 1]).max() < 1e3):
+            continue            # a diverged iterate (joint speeds > 1e3 rad/s): no meaningful check
+        checked += 1
         J = 0.0
         for k in range(T):
             xn = o.step(X[k], U[k])
@@ -105,6 +111,7 @@ def _check_consistency(o, b, rg, prec):
             J += o.cost_value(X[k], U[k])
         J += o.cost_value(X[T], terminal=True)
         assert abs(J - rg["J"][i]) <= tol_J * abs(J), (i, J, rg["J"][i])
+    assert checked >= max(1, b.x0.shape[0] // 2), checked
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
