@@ -222,6 +222,34 @@ int toget_phase_cycles(to_batch b, unsigned long long* out);
 /* Number of kernels the last tosolve_batch / tosolve_batch_device launched. */
 int tolast_launch_count(to_batch b);
 
+/*
+ * Solve without allocating device memory.  The paper has no counterpart:
+ * this is for callers that cannot call cudaMalloc while they run -- a
+ * real-time control loop whose latency must stay bounded, code confined to a
+ * fixed, pre-sized memory pool, or code running while other work is being
+ * captured into a CUDA graph.
+ *
+ * The workspace comes from one static device array of
+ * TO_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library; every GPU that loads
+ * the library holds it until the process exits.  It must fit
+ * B * (T_max + 1) knot records of the problem plus per-instance bookkeeping;
+ * a larger request returns TO_ERR_BUDGET and launches nothing.  Inputs and
+ * outputs are the caller's device buffers: d_x0 (B x n float64), d_T (B int32
+ * in [1, T_max]); d_J (B float64), d_iters, d_status (B int32); d_X
+ * (B x (T_max+1) x n float64) and d_U (B x T_max x m float64) may be NULL.
+ * opts may not set forced_alpha, want_vx or profile_phases
+ * (TO_ERR_UNSUPPORTED).  The work is enqueued on cuda_stream; results are
+ * ready when the stream reaches them.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current), so make that first call before any stream capture.
+ * Every call shares the one array: calls whose work overlaps on the GPU (two
+ * streams, two host threads) race and corrupt each other; serialise them.
+ */
+#define TO_NOALLOC_SCRATCH_BYTES (64u << 20)
+int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_T, const to_solver_opts* opts,
+                          void* cuda_stream, double* d_J, int* d_iters, int* d_status, double* d_X, double* d_U);
+
 const char* tolast_error(void);
 
 #ifdef __cplusplus

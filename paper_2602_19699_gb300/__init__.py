@@ -75,6 +75,7 @@ def lib():
             L.toget_device_results.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
             L.tolast_launch_count.argtypes = [vp]
             L.toget_phase_cycles.argtypes = [vp, vp]
+            L.tosolve_batch_noalloc.argtypes = [vp, i, vp, vp, C.POINTER(to_solver_opts), vp, vp, vp, vp, vp, vp]
             L.tolast_error.restype = C.c_char_p
             L.to_default_opts.argtypes = [C.POINTER(to_solver_opts)]
             L.to_default_opts.restype = None
@@ -85,7 +86,8 @@ def lib():
 def exported_symbols():
     return ["to_default_opts", "tocreate_problem", "todestroy_problem", "tocreate_batch", "tofree_batch",
             "tosolve_batch", "tosolve_batch_device", "toget_trajectories", "toget_history",
-            "toget_device_results", "tolast_launch_count", "toget_phase_cycles", "tolast_error"]
+            "toget_device_results", "tolast_launch_count", "toget_phase_cycles", "tosolve_batch_noalloc",
+            "tolast_error"]
 
 
 def tolast_error() -> str:
@@ -205,6 +207,21 @@ def tosolve_batch_device(batch: Batch, B: int, d_x0: int, d_T: int, d_U_init: in
                                       C.c_void_p(d_forced) if d_forced else None, C.byref(opts),
                                       C.c_void_p(stream) if stream else None))
     batch.B, batch.max_iter, batch.want_vx = B, opts.max_iter, opts.want_vx
+
+
+def tosolve_batch_noalloc(problem: Problem, B: int, d_x0: int, d_T: int, d_J: int, d_iters: int, d_status: int,
+                          d_X: int | None = None, d_U: int | None = None, opts: to_solver_opts | None = None,
+                          stream=None):
+    """Solve without allocating device memory: the library's static workspace
+    is used and the caller's device buffers receive the results (raw device
+    pointers).  The first call on a device must come before any stream capture;
+    calls that overlap on the GPU race on the shared workspace."""
+    opts = opts if opts is not None else to_default_opts()
+    opts.forced_alpha = None
+    vp = C.c_void_p
+    _check(lib().tosolve_batch_noalloc(problem.handle, int(B), vp(d_x0), vp(d_T), C.byref(opts),
+                                       vp(stream) if stream else None, vp(d_J), vp(d_iters), vp(d_status),
+                                       vp(d_X) if d_X else None, vp(d_U) if d_U else None))
 
 
 def toget_trajectories(batch: Batch, X=True, U=True, Vx=False, K=False) -> dict:

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "launch.cuh"
@@ -584,3 +585,107 @@ int toget_history(to_batch b, int* alpha_idx, double* J_hist) {
   return TO_OK;
 }
 
+
+// ===========================================================================
+// Solve without any device allocation.
+//
+// For callers that must not allocate device memory while they run: a
+// real-time control loop that has to keep its latency bounded, a process
+// that works inside a fixed, pre-sized memory pool, or code that runs while
+// other work is being captured into a CUDA graph.  The workspace (knot
+// offsets, horizon order, trajectory slots, gains, per-iteration history)
+// lives in one file-scope device array of TO_NOALLOC_SCRATCH_BYTES that every
+// GPU loading this library keeps until the process exits.  Inputs and outputs
+// are the caller's device buffers.
+// ===========================================================================
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[TO_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kMaxDevices] = {};   // device address of the array, per device
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_T, const to_solver_opts* opts,
+                          void* cuda_stream, double* d_J, int* d_iters, int* d_status, double* d_X, double* d_U) {
+  if (!p) return fail(TO_ERR_ARG, "tosolve_batch_noalloc: null problem");
+  to_solver_opts o;
+  to_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.forced_alpha || o.want_vx || o.profile_phases)
+    return fail(TO_ERR_UNSUPPORTED, "tosolve_batch_noalloc: forced steps, want_vx and profiling are not available");
+  int rc = check_opts(&o);
+  if (rc) return rc;
+  if (B < 0 || (B > 0 && (!d_x0 || !d_T || !d_J || !d_iters || !d_status)))
+    return fail(TO_ERR_ARG, "tosolve_batch_noalloc: x0, T, J, iters and status are required");
+  if (B == 0) return TO_OK;
+  // the device address of the array: once per device, with that device current
+  int dev = 0;
+  TO_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(TO_ERR_UNSUPPORTED, "tosolve_batch_noalloc: device index too large");
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(TO_ERR_CUDA, std::string("tosolve_batch_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_noalloc_base[dev] = ptr;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+  }
+  // carve the workspace out of the array (horizons are bounded by T_max, so
+  // B (T_max + 1) knot records always suffice)
+  const SysOps* ops = p->ops;
+  const int pi = o.prec == TO_FP64 ? 0 : 1;
+  const int elem = o.prec == TO_FP64 ? 8 : 4;
+  const long long knots = (long long)B * (p->T_max + 1);
+  const int mi = std::max(o.max_iter, 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t at = off; off = align256(off + bytes); return at; };
+  const size_t o_toff = take(sizeof(long long) * B), o_order = take(sizeof(int) * B),
+               o_hist = take(sizeof(int) * (p->T_max + 2)), o_err = take(sizeof(int)), o_queue = take(sizeof(int)),
+               o_slot = take(sizeof(int) * B), o_ahist = take(sizeof(int) * (size_t)B * mi),
+               o_jhist = take(sizeof(double) * (size_t)B * (mi + 1)),
+               o_traj = take((size_t)knots * kMaxSlots * ops->rs[pi] * elem),
+               o_gains = take((size_t)knots * ops->gs[pi] * elem);
+  if (off > TO_NOALLOC_SCRATCH_BYTES)
+    return fail(TO_ERR_BUDGET, "tosolve_batch_noalloc: needs " + std::to_string(off) + " bytes of workspace, more than "
+                                   "the static " + std::to_string((size_t)TO_NOALLOC_SCRATCH_BYTES) + " bytes");
+  to_batch_s w;
+  w.p = p;
+  w.B_max = B;
+  w.knots_max = knots;
+  w.elem_bytes = elem;
+  w.toff = reinterpret_cast<long long*>(base + o_toff);
+  w.order = reinterpret_cast<int*>(base + o_order);
+  w.hist = reinterpret_cast<int*>(base + o_hist);
+  w.err = reinterpret_cast<int*>(base + o_err);
+  w.queue = reinterpret_cast<int*>(base + o_queue);
+  w.slot = reinterpret_cast<int*>(base + o_slot);
+  w.ahist = reinterpret_cast<int*>(base + o_ahist);
+  w.Jhist = reinterpret_cast<double*>(base + o_jhist);
+  w.traj = base + o_traj;
+  w.gains = base + o_gains;
+  w.J = d_J;
+  w.iters = d_iters;
+  w.status = d_status;
+  w.hist_iter_cap = mi;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the prepare kernel resets the queue, the error flag and the histogram;
+  // every other region is written before it is read
+  rc = launch_solve(&w, B, d_x0, d_T, nullptr, nullptr, &o, s);
+  if (rc) return rc;
+  if (d_X || d_U) {
+    const int NS = std::min(w.G, kLsWidth) + 1;
+    gather_kernel<<<1024, 256, 0, s>>>(B, p->T_max, p->n, p->m, ops->rs[pi], ops->gs[pi], NS, elem, w.toff, d_T,
+                                       w.slot, w.traj, w.gains, nullptr, d_X, d_U, nullptr, nullptr);
+    TO_CK(cudaGetLastError());
+  }
+  return TO_OK;
+}
