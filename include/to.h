@@ -57,9 +57,9 @@ enum {
 enum {
   TO_FP64 = 0, /* every step in float64                                        */
   TO_MIXED = 1 /* float32 rollouts, derivatives and Riccati products; float64
-                  Q_uu Cholesky, pivot test, refinement residual and the
-                  line-search cost comparison; the cost is accumulated as a
-                  compensated float32 pair (about 48 significant bits)        */
+                  Q_uu Cholesky, pivot test and line-search cost comparison;
+                  the refinement residual of the gain solve and the cost
+                  accumulation are float-float (about 48 significant bits)    */
 };
 
 /* return codes */
@@ -143,8 +143,10 @@ typedef struct {
   int n_alpha;            /* number of step sizes L (1..32)                    */
   double alpha_decay;     /* alpha_j = alpha_decay^j                           */
   int prec;               /* TO_FP64 or TO_MIXED                               */
-  int refine;             /* mixed mode: 1 = one FP64-residual refinement step of
-                             the gain solve, 0 = none                          */
+  int refine;             /* mixed mode: one refinement step of the gain solve
+                             with the residual formed in float-float (1: exact
+                             FMA products, compensated sum, ~48 bits) or in
+                             native float64 (2); 0 = none                     */
   const int* forced_alpha;/* test hook, host B x max_iter or NULL: iteration i of
                              instance b takes step index forced_alpha[b*max_iter+i]
                              with no test; -1 ends that instance's run          */

@@ -173,6 +173,83 @@ TO_DEV void eigclip_small(R* Q, R eps) {
     }
 }
 
+// The same clip for larger blocks with runtime loops (small code; the
+// matrices live in local memory).  One thread.
+template <class R, int P>
+TO_DEV void eigclip_jacobi(R* Q, R eps) {
+  R gmax = -R(1e30);
+  for (int i = 0; i < P; ++i) {
+    R s = Q[i * P + i];
+    for (int j = 0; j < P; ++j)
+      if (j != i) s += fabs(Q[i * P + j]);
+    gmax = s > gmax ? s : gmax;
+  }
+  if (gmax <= eps) {
+    for (int i = 0; i < P * P; ++i) Q[i] = (i % (P + 1) == 0) ? eps : R(0);
+    return;
+  }
+  R A[P * P], W[P * P];
+  {
+    bool pd = true;
+    for (int j = 0; j < P && pd; ++j) {
+      R s = Q[j * P + j] - eps;
+      for (int k = 0; k < j; ++k) s -= A[j * P + k] * A[j * P + k];
+      if (!(s > R(0))) { pd = false; break; }
+      const R r = rsqrt_(s);
+      A[j * P + j] = s * r;
+      for (int i = j + 1; i < P; ++i) {
+        R t = Q[i * P + j];
+        for (int k = 0; k < j; ++k) t -= A[i * P + k] * A[j * P + k];
+        A[i * P + j] = t * r;
+      }
+    }
+    if (pd) return;
+  }
+  for (int i = 0; i < P * P; ++i) { A[i] = Q[i]; W[i] = (i % (P + 1) == 0) ? R(1) : R(0); }
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    R off = 0, tot = 0;
+    for (int p = 0; p < P; ++p)
+      for (int q = 0; q < P; ++q) {
+        tot += A[p * P + q] * A[p * P + q];
+        if (p != q) off += A[p * P + q] * A[p * P + q];
+      }
+    if (!(off > R(sizeof(R) == 4 ? 1e-14 : 1e-30) * tot)) break;
+    for (int p = 0; p < P; ++p)
+      for (int q = p + 1; q < P; ++q) {
+        const R apq = A[p * P + q];
+        if (apq == R(0)) continue;
+        const R tau = (A[q * P + q] - A[p * P + p]) / (R(2) * apq);
+        const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+        const R c = rsqrt_(R(1) + t * t), s = t * c;
+        for (int k = 0; k < P; ++k) {
+          const R akp = A[k * P + p], akq = A[k * P + q];
+          A[k * P + p] = c * akp - s * akq;
+          A[k * P + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < P; ++k) {
+          const R apk = A[p * P + k], aqk = A[q * P + k];
+          A[p * P + k] = c * apk - s * aqk;
+          A[q * P + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < P; ++k) {
+          const R wkp = W[k * P + p], wkq = W[k * P + q];
+          W[k * P + p] = c * wkp - s * wkq;
+          W[k * P + q] = s * wkp + c * wkq;
+        }
+      }
+  }
+  for (int i = 0; i < P; ++i)
+    for (int j = i; j < P; ++j) {
+      R s = 0;
+      for (int k = 0; k < P; ++k) {
+        const R d = A[k * P + k] > eps ? A[k * P + k] : eps;
+        s += W[i * P + k] * d * W[j * P + k];
+      }
+      Q[i * P + j] = s;
+      Q[j * P + i] = s;
+    }
+}
+
 // Clip of a symmetric 2x2 [a b; b c]: one Jacobi rotation diagonalises it
 // exactly (Golub & Van Loan sec. 8.5.2); the rotation is scale-free, so tiny
 // entries (far from a bump, in float32) cannot underflow into 0/0.

@@ -104,6 +104,7 @@ struct Work {
   double mu;
   double red;
   R Lf[m * m];           // the factor rounded to R, unit diagonal scaled: Lf[jj] = 1 / L_jj
+  R Quf[m * m];          // Q_uu as formed in R (float-float refinement residual)
   R V[n * n];            // V_xx, then Q_xx, then the new V_xx (in place)
   R v[n];                // V_x
   R A[n * n];
@@ -214,19 +215,45 @@ struct Solver {
       for (int i = 0; i < m; ++i) out[i] = (R)x[i];
     } else {
       // float32 triangular solves with the rounded factor, then one
-      // refinement step whose residual b - (Q_uu + mu I) x is formed in float64
+      // refinement step on the residual b - (Q_uu + mu I) x.  refine = 1
+      // forms it in float-float: Q_uu's entries and x are float32, so every
+      // product is exact as a (p, e) pair from one FMA and the sum is
+      // compensated (about 48 significant bits, float32 pipe only);
+      // refine = 2 forms it in native float64.
       float b[m], x[m];
 #pragma unroll
       for (int i = 0; i < m; ++i) b[i] = -(float)(c < n ? w.Qux[i * n + c] : w.Qu[i]);
       chol_apply<float, R>(w.Lf, b, x);
       if (refine) {
         float r[m], d[m];
+        if (refine == 2) {
 #pragma unroll
-        for (int i = 0; i < m; ++i) {
-          double t = (double)b[i] - w.mu * (double)x[i];
+          for (int i = 0; i < m; ++i) {
+            double t = (double)b[i] - w.mu * (double)x[i];
 #pragma unroll
-          for (int k = 0; k < m; ++k) t = fma(-w.Quu[i * m + k], (double)x[k], t);
-          r[i] = (float)t;
+            for (int k = 0; k < m; ++k) t = fma(-w.Quu[i * m + k], (double)x[k], t);
+            r[i] = (float)t;
+          }
+        } else {
+          const float muf = (float)w.mu;
+#pragma unroll
+          for (int i = 0; i < m; ++i) {
+            Acc<float> t;
+            t.add(b[i]);
+            if (muf != 0.f) {
+              const float p = muf * x[i];
+              t.add(-p);
+              t.add(-fmaf(muf, x[i], -p));
+            }
+#pragma unroll
+            for (int k = 0; k < m; ++k) {
+              const float q = (float)w.Quf[i * m + k];
+              const float p = q * x[k];
+              t.add(-p);
+              t.add(-fmaf(q, x[k], -p));
+            }
+            r[i] = t.hi + t.lo;
+          }
         }
         chol_apply<float, R>(w.Lf, r, d);
 #pragma unroll
@@ -324,6 +351,7 @@ struct Solver {
 #pragma unroll 6
           for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VB[r * m + j];
           w.Quu[f] = (double)s;                         // Q_uu
+          w.Quf[f] = s;
         } else if (e < NT + m * n + m * m + n) {
           const int i = e - NT - m * n - m * m;
           R s = w.lx[i];

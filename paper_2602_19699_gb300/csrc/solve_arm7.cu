@@ -1,25 +1,53 @@
-// arm7: placeholder until the system's device model lands.
-#include "launch.cuh"
+// 7-DoF serial arm: parameter parsing and solver instantiation.
+#include <cmath>
+
+#include "rigid_parse.cuh"
 
 namespace to {
 
-static int parse_arm7(const double*, size_t, std::vector<unsigned char>&, std::vector<unsigned char>&,
-                        std::string& err) {
-  err = "arm7: system not available in this build";
-  return -1;
+static int parse_arm7(const double* p, size_t np, std::vector<unsigned char>& blob64, std::vector<unsigned char>& blob32,
+                      std::string& err) {
+  RigidHeader h;
+  if (!parse_rigid(p, np, h, err)) return -1;
+  RigidParams<double, 7> P{};
+  if (!fill_rigid<7>(h, 0, P, err)) return -1;
+  for (int i = 0; i < 7; ++i)
+    if (h.bodies[i].parent != i - 1 || h.bodies[i].jtype > 2) {
+      err = "arm7 params: joints must be a chain of revolute joints";
+      return -1;
+    }
+  if (h.n_cost < 11) { err = "arm7 params: cost block truncated"; return -1; }
+  const double* c = h.cost;
+  P.wtau = c[0]; P.wv = c[1];
+  P.tgt[0] = c[2]; P.tgt[1] = c[3]; P.tgt[2] = c[4];
+  P.wee = c[5]; P.wvT = c[6];
+  P.ee_body = (int)c[7];
+  P.ee_pt[0] = c[8]; P.ee_pt[1] = c[9]; P.ee_pt[2] = c[10];
+  if (P.ee_body < 0 || P.ee_body >= 7) { err = "arm7 params: bad end-effector body"; return -1; }
+  P.nfeet = 0;
+  to_blobs<RigidArm7P>(P, blob64, blob32);
+  return 0;
 }
 
-static cudaError_t launch_none(int, int, int, int, cudaStream_t, const SolveArgs&) { return cudaErrorNotSupported; }
-static cudaError_t occ_none(int, int, int, size_t*, int*) { return cudaErrorNotSupported; }
+typedef Dispatch<SysArm7, 32> A7Dispatch;
+
+static SysOps make_ops() {
+  SysOps o{};
+  o.sys = 3;
+  fill_layout<SysArm7>(o);
+  o.n_groups = 1;
+  o.groups[0] = 32;
+  o.default_G = 32;
+  o.default_gpb[0] = 2; o.default_gpb[1] = 2;
+  o.accepts_actor = false;
+  o.parse = parse_arm7;
+  o.launch = A7Dispatch::launch;
+  o.occupancy = A7Dispatch::occupancy;
+  return o;
+}
 
 const SysOps& arm7_ops() {
-  static SysOps o = [] {
-    SysOps x{};
-    x.parse = parse_arm7;
-    x.launch = launch_none;
-    x.occupancy = occ_none;
-    return x;
-  }();
+  static SysOps o = make_ops();
   return o;
 }
 

@@ -1,25 +1,53 @@
-// quad: placeholder until the system's device model lands.
-#include "launch.cuh"
+// Quadruped-shaped floating base: parameter parsing and solver instantiation.
+#include <cmath>
+
+#include "rigid_parse.cuh"
 
 namespace to {
 
-static int parse_quad(const double*, size_t, std::vector<unsigned char>&, std::vector<unsigned char>&,
-                        std::string& err) {
-  err = "quad: system not available in this build";
-  return -1;
+static int parse_quad(const double* p, size_t np, std::vector<unsigned char>& blob64, std::vector<unsigned char>& blob32,
+                      std::string& err) {
+  RigidHeader h;
+  if (!parse_rigid(p, np, h, err)) return -1;
+  RigidParams<double, 18> P{};
+  if (!fill_rigid<18>(h, 6, P, err)) return -1;
+  if (h.n_cost < 11) { err = "quad params: cost block truncated"; return -1; }
+  const double* c = h.cost;
+  P.wtau = c[0]; P.znom = c[1]; P.wz = c[2]; P.wrpy = c[3]; P.wvx = c[4]; P.vxt = c[5];
+  P.tscale = c[6]; P.kc = c[7]; P.dc = c[8]; P.beta = c[9];
+  P.nfeet = (int)c[10];
+  if (P.nfeet < 0 || P.nfeet > 4 || h.n_cost < (size_t)(11 + 4 * P.nfeet) || !(P.beta > 0)) {
+    err = "quad params: bad contact block";
+    return -1;
+  }
+  for (int f = 0; f < P.nfeet; ++f) {
+    P.foot_body[f] = (int)c[11 + 4 * f];
+    if (P.foot_body[f] < 0 || P.foot_body[f] >= 18) { err = "quad params: bad foot body"; return -1; }
+    for (int k = 0; k < 3; ++k) P.foot_pt[f][k] = c[12 + 4 * f + k];
+  }
+  to_blobs<RigidQuadP>(P, blob64, blob32);
+  return 0;
 }
 
-static cudaError_t launch_none(int, int, int, int, cudaStream_t, const SolveArgs&) { return cudaErrorNotSupported; }
-static cudaError_t occ_none(int, int, int, size_t*, int*) { return cudaErrorNotSupported; }
+typedef Dispatch<SysQuad, 64> QDispatch;
+
+static SysOps make_ops() {
+  SysOps o{};
+  o.sys = 4;
+  fill_layout<SysQuad>(o);
+  o.n_groups = 1;
+  o.groups[0] = 64;
+  o.default_G = 64;
+  o.default_gpb[0] = 1; o.default_gpb[1] = 1;
+  o.accepts_actor = false;
+  o.parse = parse_quad;
+  o.launch = QDispatch::launch;
+  o.occupancy = QDispatch::occupancy;
+  return o;
+}
 
 const SysOps& quad_ops() {
-  static SysOps o = [] {
-    SysOps x{};
-    x.parse = parse_quad;
-    x.launch = launch_none;
-    x.occupancy = occ_none;
-    return x;
-  }();
+  static SysOps o = make_ops();
   return o;
 }
 

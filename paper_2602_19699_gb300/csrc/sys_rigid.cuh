@@ -1,0 +1,538 @@
+// Rigid-body trees for the 7-DoF arm and the quadruped-shaped floating base
+// (Sec. V-A's manipulators, Sec. V-D's quadruped; the synthetic workloads'
+// parameters).  x = [q; qd], u = torques of joints a0..N-1.
+//
+// Dynamics: M(q) qdd + h(q, qd) = [0; u] (+ soft ground contact at the feet
+// for the quadruped), n_sub semi-implicit Euler substeps of h = dt / n_sub:
+//   qd+ = qd + h qdd,  q+ = q + h qd+.
+// * h(q, qd): body-frame spatial Newton-Euler (Featherstone 2008, ch. 5) with
+//   gravity as a base acceleration and the contact forces as external forces;
+// * M(q): columns from Newton-Euler at unit accelerations, zero velocity,
+//   no gravity, no contact; Cholesky-factored.
+// Derivatives: each lane propagates one tangent direction (a state
+// coordinate, or a control) through the substeps:
+//   dqdd = M^{-1} (dtau - d ID(q, qd, qdd) / d(q, qd) . (dq, dqd)),
+// with the directional derivative of the inverse dynamics (qdd held fixed)
+// from a dual-number pass of the same Newton-Euler code.
+#pragma once
+#include "common.cuh"
+
+namespace to {
+
+// ---------------------------------------------------------------------------
+// a dual number: value and one directional derivative
+// ---------------------------------------------------------------------------
+template <class R>
+struct Dl {
+  R v, d;
+  TO_DEV Dl() {}
+  TO_DEV Dl(R a) : v(a), d(0) {}
+  TO_DEV Dl(R a, R b) : v(a), d(b) {}
+};
+template <class R> TO_DEV Dl<R> operator+(Dl<R> a, Dl<R> b) { return Dl<R>(a.v + b.v, a.d + b.d); }
+template <class R> TO_DEV Dl<R> operator-(Dl<R> a, Dl<R> b) { return Dl<R>(a.v - b.v, a.d - b.d); }
+template <class R> TO_DEV Dl<R> operator-(Dl<R> a) { return Dl<R>(-a.v, -a.d); }
+template <class R> TO_DEV Dl<R> operator*(Dl<R> a, Dl<R> b) { return Dl<R>(a.v * b.v, a.v * b.d + a.d * b.v); }
+template <class R> TO_DEV Dl<R> operator*(R a, Dl<R> b) { return Dl<R>(a * b.v, a * b.d); }
+template <class R> TO_DEV Dl<R> operator/(Dl<R> a, Dl<R> b) {
+  const R iv = R(1) / b.v;
+  return Dl<R>(a.v * iv, (a.d - a.v * iv * b.d) * iv);
+}
+template <class R> TO_DEV Dl<R>& operator+=(Dl<R>& a, Dl<R> b) { a = a + b; return a; }
+template <class R> TO_DEV Dl<R>& operator-=(Dl<R>& a, Dl<R> b) { a = a - b; return a; }
+TO_DEV float dexp(float a) { return expf(a); }
+TO_DEV double dexp(double a) { return exp(a); }
+TO_DEV float dlog1p(float a) { return log1pf(a); }
+TO_DEV double dlog1p(double a) { return log1p(a); }
+TO_DEV void dsincos(float a, float* s, float* c) { sincosf(a, s, c); }
+TO_DEV void dsincos(double a, double* s, double* c) { sincos(a, s, c); }
+template <class R> TO_DEV Dl<R> dexp(Dl<R> a) { const R e = dexp(a.v); return Dl<R>(e, e * a.d); }
+template <class R> TO_DEV Dl<R> dlog1p(Dl<R> a) { return Dl<R>(dlog1p(a.v), a.d / (R(1) + a.v)); }
+template <class R> TO_DEV void dsincos(Dl<R> a, Dl<R>* s, Dl<R>* c) {
+  R sv, cv;
+  dsincos(a.v, &sv, &cv);
+  *s = Dl<R>(sv, cv * a.d);
+  *c = Dl<R>(cv, -(sv * a.d));
+}
+
+// ---------------------------------------------------------------------------
+// parameters
+// ---------------------------------------------------------------------------
+enum { RK_ARM7 = 3, RK_QUAD = 4 };
+
+template <class R, int N>
+struct RigidParams {
+  R dt, g[3];
+  int n_sub, a0;
+  int parent[N], jtype[N];
+  R off[N][3], mass[N], com[N][3], inertia[N][3];
+  // arm reaching cost
+  R wtau, wv, tgt[3], wee, wvT, ee_pt[3];
+  int ee_body;
+  // quadruped cost and contact
+  R znom, wz, wrpy, wvx, vxt, tscale, kc, dc, beta;
+  int nfeet, foot_body[4];
+  R foot_pt[4][3];
+};
+
+template <class D, class S, int N>
+inline void cast_params(const RigidParams<S, N>& s, RigidParams<D, N>& d) {
+  d.dt = (D)s.dt;
+  for (int k = 0; k < 3; ++k) { d.g[k] = (D)s.g[k]; d.tgt[k] = (D)s.tgt[k]; d.ee_pt[k] = (D)s.ee_pt[k]; }
+  d.n_sub = s.n_sub; d.a0 = s.a0;
+  for (int i = 0; i < N; ++i) {
+    d.parent[i] = s.parent[i]; d.jtype[i] = s.jtype[i]; d.mass[i] = (D)s.mass[i];
+    for (int k = 0; k < 3; ++k) { d.off[i][k] = (D)s.off[i][k]; d.com[i][k] = (D)s.com[i][k]; d.inertia[i][k] = (D)s.inertia[i][k]; }
+  }
+  d.wtau = (D)s.wtau; d.wv = (D)s.wv; d.wee = (D)s.wee; d.wvT = (D)s.wvT; d.ee_body = s.ee_body;
+  d.znom = (D)s.znom; d.wz = (D)s.wz; d.wrpy = (D)s.wrpy; d.wvx = (D)s.wvx; d.vxt = (D)s.vxt;
+  d.tscale = (D)s.tscale; d.kc = (D)s.kc; d.dc = (D)s.dc; d.beta = (D)s.beta; d.nfeet = s.nfeet;
+  for (int f = 0; f < 4; ++f) {
+    d.foot_body[f] = s.foot_body[f];
+    for (int k = 0; k < 3; ++k) d.foot_pt[f][k] = (D)s.foot_pt[f][k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the model
+// ---------------------------------------------------------------------------
+template <int N_, int A0, int KIND>
+struct SysRigid {
+  static constexpr int N = N_;
+  static constexpr int n = 2 * N, m = N - A0;
+  template <class R> using ParamsT = RigidParams<R, N>;
+
+  // 3-vectors
+  template <class S> TO_DEV static void cross(const S* a, const S* b, S* c) {
+    const S c0 = a[1] * b[2] - a[2] * b[1], c1 = a[2] * b[0] - a[0] * b[2], c2 = a[0] * b[1] - a[1] * b[0];
+    c[0] = c0; c[1] = c1; c[2] = c2;
+  }
+  // y = E x and y = E^T x for a row-major 3x3 E
+  template <class S> TO_DEV static void mv(const S* E, const S* x, S* y) {
+    const S y0 = E[0] * x[0] + E[1] * x[1] + E[2] * x[2];
+    const S y1 = E[3] * x[0] + E[4] * x[1] + E[5] * x[2];
+    const S y2 = E[6] * x[0] + E[7] * x[1] + E[8] * x[2];
+    y[0] = y0; y[1] = y1; y[2] = y2;
+  }
+  template <class S> TO_DEV static void mtv(const S* E, const S* x, S* y) {
+    const S y0 = E[0] * x[0] + E[3] * x[1] + E[6] * x[2];
+    const S y1 = E[1] * x[0] + E[4] * x[1] + E[7] * x[2];
+    const S y2 = E[2] * x[0] + E[5] * x[1] + E[8] * x[2];
+    y[0] = y0; y[1] = y1; y[2] = y2;
+  }
+
+  // Plucker transform of joint i: E maps parent coordinates to body
+  // coordinates (a rotation by q about the joint axis, or identity), r is the
+  // body origin in parent coordinates
+  template <class R, class S>
+  TO_DEV static void joint_transform(const ParamsT<R>& P, int i, S q, S* E, S* r) {
+    const int jt = P.jtype[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = S(P.off[i][k]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) E[k] = S(R(0));
+    if (jt <= 2) {
+      S s, c;
+      dsincos(q, &s, &c);
+      const int a = jt, b = (jt + 1) % 3, cc = (jt + 2) % 3;
+      E[a * 3 + a] = S(R(1));
+      E[b * 3 + b] = c; E[b * 3 + cc] = s;
+      E[cc * 3 + b] = -s; E[cc * 3 + cc] = c;
+    } else {
+      E[0] = S(R(1)); E[4] = S(R(1)); E[8] = S(R(1));
+      r[jt - 3] = r[jt - 3] + q;
+    }
+  }
+
+  // world pose: E0 maps world to body coordinates, p0 is the body origin
+  template <class R, class S>
+  TO_DEV static void world_pose(const ParamsT<R>& P, const S* q, S (*E0)[9], S (*p0)[3]) {
+    for (int i = 0; i < N; ++i) {
+      S E[9], r[3];
+      joint_transform(P, i, q[i], E, r);
+      const int pa = P.parent[i];
+      if (pa < 0) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) E0[i][k] = E[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p0[i][k] = r[k];
+      } else {
+        // E0_i = E E0_p ;  p0_i = p0_p + E0_p^T r
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            E0[i][a * 3 + b] = E[a * 3 + 0] * E0[pa][0 * 3 + b] + E[a * 3 + 1] * E0[pa][1 * 3 + b] + E[a * 3 + 2] * E0[pa][2 * 3 + b];
+        S wr[3];
+        mtv(E0[pa], r, wr);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p0[i][k] = p0[pa][k] + wr[k];
+      }
+    }
+  }
+
+  // spatial inertia times a motion vector (w, v): momentum about the body
+  // origin, (I_c w + c x p, p) with p = m (v + w x c)
+  template <class R, class S>
+  TO_DEV static void inertia_mul(const ParamsT<R>& P, int i, const S* w, const S* v, S* n, S* f) {
+    S c[3] = {S(P.com[i][0]), S(P.com[i][1]), S(P.com[i][2])};
+    S wc[3];
+    cross(w, c, wc);
+    S p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = P.mass[i] * (v[k] + wc[k]);
+    S cp[3];
+    cross(c, p, cp);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { n[k] = P.inertia[i][k] * w[k] + cp[k]; f[k] = p[k]; }
+  }
+
+  // inverse dynamics: tau = ID(q, qd, qdd) with optional gravity and contact
+  template <class R, class S>
+  TO_DEV static void rnea(const ParamsT<R>& P, const S* q, const S* qd, const S* qdd, bool grav, bool contact,
+                          S* tau) {
+    S E[N][9], r[N][3], vw[N][3], vv[N][3], fn[N][3], ff[N][3];
+    S aw[3], av[3];
+    S E0[KIND == RK_QUAD ? N : 1][9], p0[KIND == RK_QUAD ? N : 1][3];
+    S awb[N][3], avb[N][3];
+    for (int i = 0; i < N; ++i) {
+      joint_transform(P, i, q[i], E[i], r[i]);
+      const int pa = P.parent[i];
+      S pw[3], pv[3], paw[3], pav[3];
+      if (pa < 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          pw[k] = S(R(0)); pv[k] = S(R(0)); paw[k] = S(R(0));
+          pav[k] = grav ? S(-P.g[k]) : S(R(0));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          pw[k] = vw[pa][k]; pv[k] = vv[pa][k]; paw[k] = awb[pa][k]; pav[k] = avb[pa][k];
+        }
+      }
+      // X m = (E w, E (v - r x w))
+      S t[3], rw[3];
+      cross(r[i], pw, rw);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t[k] = pv[k] - rw[k];
+      mv(E[i], pw, vw[i]);
+      mv(E[i], t, vv[i]);
+      cross(r[i], paw, rw);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
+      mv(E[i], paw, aw);
+      mv(E[i], t, av);
+      // joint motion S qd, S qdd; velocity-product term v x (S qd)
+      const int jt = P.jtype[i];
+      S sw[3] = {S(R(0)), S(R(0)), S(R(0))}, sv[3] = {S(R(0)), S(R(0)), S(R(0))};
+      if (jt <= 2) sw[jt] = qd[i]; else sv[jt - 3] = qd[i];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { vw[i][k] = vw[i][k] + sw[k]; vv[i][k] = vv[i][k] + sv[k]; }
+      S c1[3], c2[3], c3[3];
+      cross(vw[i], sw, c1);
+      cross(vw[i], sv, c2);
+      cross(vv[i], sw, c3);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { aw[k] = aw[k] + c1[k]; av[k] = av[k] + c2[k] + c3[k]; }
+      if (jt <= 2) aw[jt] = aw[jt] + qdd[i]; else av[jt - 3] = av[jt - 3] + qdd[i];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { awb[i][k] = aw[k]; avb[i][k] = av[k]; }
+      // f = I a + v x* (I v)
+      S In[3], If[3], hn[3], hf[3];
+      inertia_mul(P, i, aw, av, In, If);
+      inertia_mul(P, i, vw[i], vv[i], hn, hf);
+      S x1[3], x2[3], x3[3];
+      cross(vw[i], hn, x1);
+      cross(vv[i], hf, x2);
+      cross(vw[i], hf, x3);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { fn[i][k] = In[k] + x1[k] + x2[k]; ff[i][k] = If[k] + x3[k]; }
+      if (KIND == RK_QUAD) {
+        if (pa < 0) {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) E0[i][k] = E[i][k];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) p0[i][k] = r[i][k];
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+              E0[i][a * 3 + b] = E[i][a * 3 + 0] * E0[pa][b] + E[i][a * 3 + 1] * E0[pa][3 + b] + E[i][a * 3 + 2] * E0[pa][6 + b];
+          S wr[3];
+          mtv(E0[pa], r[i], wr);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) p0[i][k] = p0[pa][k] + wr[k];
+        }
+      }
+    }
+    if (KIND == RK_QUAD && contact) {
+      for (int ft = 0; ft < P.nfeet; ++ft) {
+        const int bi = P.foot_body[ft];
+        S pt[3] = {S(P.foot_pt[ft][0]), S(P.foot_pt[ft][1]), S(P.foot_pt[ft][2])};
+        S wpt[3], Pw[3], wxp[3], vb[3], vwld[3];
+        mtv(E0[bi], pt, wpt);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Pw[k] = p0[bi][k] + wpt[k];
+        cross(vw[bi], pt, wxp);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) vb[k] = vv[bi][k] + wxp[k];
+        mtv(E0[bi], vb, vwld);
+        // normal: k softplus_beta(-z) - d sigmoid(-beta z) zdot; tangential damper
+        const S bz = P.beta * Pw[2];
+        const S ebz = dexp(bz);
+        const S sp = (R(1) / P.beta) * dlog1p(S(R(1)) / ebz);
+        const S gate = S(R(1)) / (S(R(1)) + ebz);
+        S F[3];
+        F[0] = -(P.dc * (gate * vwld[0]));
+        F[1] = -(P.dc * (gate * vwld[1]));
+        F[2] = P.kc * sp - P.dc * (gate * vwld[2]);
+        S mw[3], mb[3], fb[3];
+        cross(wpt, F, mw);
+        mv(E0[bi], mw, mb);
+        mv(E0[bi], F, fb);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { fn[bi][k] = fn[bi][k] - mb[k]; ff[bi][k] = ff[bi][k] - fb[k]; }
+      }
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      const int jt = P.jtype[i];
+      tau[i] = jt <= 2 ? fn[i][jt] : ff[i][jt - 3];
+      const int pa = P.parent[i];
+      if (pa >= 0) {
+        // X^T f = (E^T n + r x E^T f, E^T f)
+        S en[3], ef[3], rf[3];
+        mtv(E[i], fn[i], en);
+        mtv(E[i], ff[i], ef);
+        cross(r[i], ef, rf);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { fn[pa][k] = fn[pa][k] + en[k] + rf[k]; ff[pa][k] = ff[pa][k] + ef[k]; }
+      }
+    }
+  }
+
+  // mass matrix columns from unit accelerations; Cholesky with reciprocal pivots
+  template <class R>
+  TO_DEV static void mass_chol(const ParamsT<R>& P, const R* q, R* L) {
+    R z[N], e[N], col[N];
+    for (int i = 0; i < N; ++i) z[i] = R(0);
+    for (int j = 0; j < N; ++j) {
+      for (int i = 0; i < N; ++i) e[i] = (i == j) ? R(1) : R(0);
+      rnea<R, R>(P, q, z, e, false, false, col);
+      for (int i = j; i < N; ++i) L[i * N + j] = col[i];
+    }
+    for (int j = 0; j < N; ++j) {
+      R s = L[j * N + j];
+      for (int k = 0; k < j; ++k) s -= L[j * N + k] * L[j * N + k];
+      const R rr = rsqrt_(s);
+      L[j * N + j] = rr;
+      for (int i = j + 1; i < N; ++i) {
+        R t = L[i * N + j];
+        for (int k = 0; k < j; ++k) t -= L[i * N + k] * L[j * N + k];
+        L[i * N + j] = t * rr;
+      }
+    }
+  }
+  template <class R>
+  TO_DEV static void chol_solve(const R* L, const R* b, R* x) {
+    R y[N];
+    for (int i = 0; i < N; ++i) {
+      R t = b[i];
+      for (int k = 0; k < i; ++k) t -= L[i * N + k] * y[k];
+      y[i] = t * L[i * N + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      R t = y[i];
+      for (int k = i + 1; k < N; ++k) t -= L[k * N + i] * x[k];
+      x[i] = t * L[i * N + i];
+    }
+  }
+
+  // one substep's acceleration: qdd = M^{-1} (tau - h); also returns L
+  template <class R>
+  TO_DEV static void accel(const ParamsT<R>& P, const R* q, const R* qd, const R* tau, R* qdd, R* L) {
+    R z[N], h[N], rhs[N];
+    for (int i = 0; i < N; ++i) z[i] = R(0);
+    rnea<R, R>(P, q, qd, z, true, KIND == RK_QUAD, h);
+    mass_chol(P, q, L);
+    for (int i = 0; i < N; ++i) rhs[i] = tau[i] - h[i];
+    chol_solve(L, rhs, qdd);
+  }
+
+  template <class R>
+  TO_DEV static void step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {
+    R q[N], qd[N], tau[N], qdd[N], L[N * N];
+    for (int i = 0; i < N; ++i) { q[i] = x[i]; qd[i] = x[N + i]; tau[i] = i < A0 ? R(0) : u[i - A0]; }
+    const R h = P.dt / (R)P.n_sub;
+    for (int s = 0; s < P.n_sub; ++s) {
+      accel(P, q, qd, tau, qdd, L);
+      for (int i = 0; i < N; ++i) {
+        qd[i] = qd[i] + h * qdd[i];
+        q[i] = q[i] + h * qd[i];
+      }
+    }
+    for (int i = 0; i < N; ++i) { xn[i] = q[i]; xn[N + i] = qd[i]; }
+  }
+
+  // ---- costs ----
+  template <class R, class S>
+  TO_DEV static void ee_world(const ParamsT<R>& P, const S* q, S* ee) {
+    S E0[N][9], p0[N][3];
+    world_pose(P, q, E0, p0);
+    const int b = P.ee_body;
+    S pt[3] = {S(P.ee_pt[0]), S(P.ee_pt[1]), S(P.ee_pt[2])}, w[3];
+    mtv(E0[b], pt, w);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ee[k] = p0[b][k] + w[k];
+  }
+
+  template <class R>
+  TO_DEV static R running_cost(const ParamsT<R>& P, const R* x, const R* u) {
+    R l = 0;
+    for (int j = 0; j < m; ++j) l += P.wtau * u[j] * u[j];
+    if (KIND == RK_ARM7) {
+      for (int j = 0; j < N; ++j) l += P.wv * x[N + j] * x[N + j];
+    } else {
+      const R dz = x[2] - P.znom, dv = x[N] - P.vxt;
+      l += P.wz * dz * dz + P.wrpy * (x[3] * x[3] + x[4] * x[4] + x[5] * x[5]) + P.wvx * dv * dv;
+    }
+    return l;
+  }
+  template <class R>
+  TO_DEV static R cost_step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {
+    const R l = running_cost(P, x, u);
+    step(P, x, u, xn);
+    return l;
+  }
+  template <class R>
+  TO_DEV static R terminal_cost(const ParamsT<R>& P, const R* x) {
+    R l = 0;
+    if (KIND == RK_ARM7) {
+      R ee[3];
+      ee_world(P, x, ee);
+      for (int k = 0; k < 3; ++k) { const R d = ee[k] - P.tgt[k]; l += P.wee * d * d; }
+      for (int j = 0; j < N; ++j) l += P.wvT * x[N + j] * x[N + j];
+    } else {
+      const R dz = x[2] - P.znom, dv = x[N] - P.vxt;
+      l = P.tscale * (P.wz * dz * dz + P.wrpy * (x[3] * x[3] + x[4] * x[4] + x[5] * x[5]) + P.wvx * dv * dv);
+    }
+    return l;
+  }
+
+  // separable running costs: the clipped Hessians are diagonal, max(d, eps)
+  template <class R>
+  TO_DEV static void running_derivs(const ParamsT<R>& P, const R* x, const R* u, R eps, R* lxx, R* lx, R* luu,
+                                    R* lu) {
+    for (int i = 0; i < n * n; ++i) lxx[i] = 0;
+    for (int i = 0; i < m * m; ++i) luu[i] = 0;
+    for (int i = 0; i < n; ++i) lx[i] = 0;
+    const R w2 = R(2) * P.wtau;
+    for (int j = 0; j < m; ++j) { lu[j] = w2 * u[j]; luu[j * m + j] = w2 > eps ? w2 : eps; }
+    R dq[N];   // diagonal of the q-block and qd-block
+    for (int i = 0; i < n; ++i) lxx[i * n + i] = eps;
+    if (KIND == RK_ARM7) {
+      const R v2 = R(2) * P.wv;
+      for (int j = 0; j < N; ++j) { lx[N + j] = v2 * x[N + j]; lxx[(N + j) * n + N + j] = v2 > eps ? v2 : eps; }
+    } else {
+      const R z2 = R(2) * P.wz, r2 = R(2) * P.wrpy, x2 = R(2) * P.wvx;
+      lx[2] = z2 * (x[2] - P.znom); lxx[2 * n + 2] = z2 > eps ? z2 : eps;
+      for (int k = 3; k < 6; ++k) { lx[k] = r2 * x[k]; lxx[k * n + k] = r2 > eps ? r2 : eps; }
+      lx[N] = x2 * (x[N] - P.vxt); lxx[N * n + N] = x2 > eps ? x2 : eps;
+    }
+    (void)dq;
+  }
+
+  // terminal-cost derivatives; the arm's end-effector term through forward
+  // kinematics: gradient and exact Hessian by nested dual numbers (one lane),
+  // then the q-block is eigen-clipped
+  template <class R>
+  TO_DEV static void terminal_derivs(const ParamsT<R>& P, const R* x, R eps, R* lxx, R* lx) {
+    for (int i = 0; i < n * n; ++i) lxx[i] = 0;
+    for (int i = 0; i < n; ++i) lx[i] = 0;
+    if (KIND == RK_ARM7) {
+      typedef Dl<Dl<R>> H;
+      R Q[N * N];
+      for (int a = 0; a < N; ++a)
+        for (int b = a; b < N; ++b) {
+          H q[N];
+          for (int k = 0; k < N; ++k) q[k] = H(Dl<R>(x[k], k == a ? R(1) : R(0)), Dl<R>(k == b ? R(1) : R(0), R(0)));
+          H ee[3];
+          ee_world(P, q, ee);
+          H l(Dl<R>(R(0)));
+          const H wee(Dl<R>(P.wee));
+          for (int k = 0; k < 3; ++k) {
+            const H d = ee[k] - H(Dl<R>(P.tgt[k]));
+            l = l + wee * (d * d);
+          }
+          Q[a * N + b] = l.d.d;
+          Q[b * N + a] = l.d.d;
+          if (a == b) lx[a] = l.v.d;
+        }
+      eigclip_jacobi<R, N>(Q, eps);
+      for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) lxx[a * n + b] = Q[a * N + b];
+      const R v2 = R(2) * P.wvT;
+      for (int j = 0; j < N; ++j) { lx[N + j] = v2 * x[N + j]; lxx[(N + j) * n + N + j] = v2 > eps ? v2 : eps; }
+    } else {
+      const R s = P.tscale;
+      const R z2 = R(2) * P.wz * s, r2 = R(2) * P.wrpy * s, x2 = R(2) * P.wvx * s;
+      for (int i = 0; i < n; ++i) lxx[i * n + i] = eps;
+      lx[2] = z2 * (x[2] - P.znom); lxx[2 * n + 2] = z2 > eps ? z2 : eps;
+      for (int k = 3; k < 6; ++k) { lx[k] = r2 * x[k]; lxx[k * n + k] = r2 > eps ? r2 : eps; }
+      lx[N] = x2 * (x[N] - P.vxt); lxx[N * n + N] = x2 > eps ? x2 : eps;
+    }
+  }
+
+  // Columns of [A | B]: lane c < n propagates the tangent e_c of the state,
+  // lane n + j the tangent of control j, through the n_sub substeps.  The
+  // last lane also writes the (separable) running-cost derivatives.
+  template <class R, int G>
+  TO_DEV static void derivs(const ParamsT<R>& P, const Group<G>& g, const R* x, const R* u, R eps, R* A, R* B,
+                            R* lxx, R* lx, R* luu, R* lu, R*) {
+    static_assert(G >= n + m, "one lane per tangent direction");
+    const int c = g.lane;
+    if (c < n + m) {
+      R q[N], qd[N], tau[N], dq[N], dqd[N];
+      for (int i = 0; i < N; ++i) {
+        q[i] = x[i]; qd[i] = x[N + i]; tau[i] = i < A0 ? R(0) : u[i - A0];
+        dq[i] = (c == i) ? R(1) : R(0);
+        dqd[i] = (c == N + i) ? R(1) : R(0);
+      }
+      const R h = P.dt / (R)P.n_sub;
+      for (int s = 0; s < P.n_sub; ++s) {
+        R qdd[N], L[N * N];
+        accel(P, q, qd, tau, qdd, L);
+        // directional derivative of ID at fixed qdd
+        Dl<R> Dq[N], Dqd[N], Dqdd[N], Dtau[N];
+        for (int i = 0; i < N; ++i) { Dq[i] = Dl<R>(q[i], dq[i]); Dqd[i] = Dl<R>(qd[i], dqd[i]); Dqdd[i] = Dl<R>(qdd[i], R(0)); }
+        rnea<R, Dl<R>>(P, Dq, Dqd, Dqdd, true, KIND == RK_QUAD, Dtau);
+        R rhs[N], dqdd[N];
+        for (int i = 0; i < N; ++i) rhs[i] = ((c >= n && i == A0 + (c - n)) ? R(1) : R(0)) - Dtau[i].d;
+        chol_solve(L, rhs, dqdd);
+        for (int i = 0; i < N; ++i) {
+          qd[i] = qd[i] + h * qdd[i];
+          q[i] = q[i] + h * qd[i];
+          dqd[i] = dqd[i] + h * dqdd[i];
+          dq[i] = dq[i] + h * dqd[i];
+        }
+      }
+      if (c < n) {
+        for (int i = 0; i < N; ++i) { A[i * n + c] = dq[i]; A[(N + i) * n + c] = dqd[i]; }
+      } else {
+        for (int i = 0; i < N; ++i) { B[i * m + (c - n)] = dq[i]; B[(N + i) * m + (c - n)] = dqd[i]; }
+      }
+    }
+    if (c == G - 1) running_derivs(P, x, u, eps, lxx, lx, luu, lu);
+  }
+};
+
+typedef SysRigid<7, 0, RK_ARM7> SysArm7;
+typedef SysRigid<18, 6, RK_QUAD> SysQuad;
+
+}  // namespace to
+
+namespace to {
+template <class R> using RigidArm7P = RigidParams<R, 7>;
+template <class R> using RigidQuadP = RigidParams<R, 18>;
+}  // namespace to

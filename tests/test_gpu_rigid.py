@@ -1,0 +1,72 @@
+"""Parity of the rigid-body-tree systems (7-DoF arm, quadruped-shaped floating
+base with soft contact and 10 substeps per knot) with the FP64 oracle, under
+the oracle's own replayed step sequence; same tolerances and conditioning
+rule as the planar cases (see test_gpu_parity.py)."""
+import numpy as np
+import pytest
+
+from paper_2602_19699_gb300 import workload as W
+from test_gpu_parity import _check, _check_consistency, _sensitivity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2602_19699_gb300 as P
+    P.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return P
+
+
+def _solver(P, prob, T_max, prec):
+    s = P.Solver.__new__(P.Solver)
+    s.prob = prob
+    s.T_max = T_max
+    s.problem = P.tocreate_problem(prob.sys, prob.params, T_max)     # zero-control warm start
+    s.opts = P.to_default_opts(prec=prec)
+    s.batch = None
+    s._cap = (0, 0, P.TO_MIXED)
+    return s
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_arm7_replay(P, oracle_mod, prec):
+    prob = W.arm7(seed=1)
+    b = W.make_batch(prob, 8, seed=3, T=(20, 60))
+    o = oracle_mod.Oracle.from_problem(prob)
+    iters = 12 if prec == "fp64" else 3      # float32 needs a well-conditioned (short) replay
+    ro = o.solve(b.x0, b.T, max_iter=iters, tol=1e-8)
+    kappa = _sensitivity(o, b, ro, iters)
+    s = _solver(P, prob, 64, P.TO_FP64 if prec == "fp64" else P.TO_MIXED)
+    rg = s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=iters)
+    well = _check(ro, rg, kappa, prec, b.T)
+    assert well.mean() >= 0.25
+    _check_consistency(o, b, rg, prec, min_checked=4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_quad_replay(P, oracle_mod, prec):
+    prob = W.quad(seed=2, with_actor=False)
+    b = W.make_batch(prob, 2, seed=1, T=8)
+    o = oracle_mod.Oracle.from_problem(prob)
+    ro = o.solve(b.x0, b.T, max_iter=3, tol=1e-8)
+    kappa = _sensitivity(o, b, ro, 3)
+    s = _solver(P, prob, 8, P.TO_FP64 if prec == "fp64" else P.TO_MIXED)
+    rg = s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=3)
+    _check(ro, rg, kappa, prec, b.T)
+    _check_consistency(o, b, rg, prec, min_checked=1)
+
+
+def test_quad_warm_start_rollout(P, oracle_mod):
+    """max_iter = 0: the zero-control rollout through 10 substeps of contact dynamics."""
+    prob = W.quad(seed=3, with_actor=False)
+    b = W.make_batch(prob, 4, seed=2, T=20)
+    o = oracle_mod.Oracle.from_problem(prob)
+    s = _solver(P, prob, 20, P.TO_FP64)
+    rg = s.solve(b.x0, b.T, max_iter=0)
+    for i in range(4):
+        X, J = o.rollout(b.x0[i], np.zeros((20, 12)))
+        assert np.abs(rg["X"][i] - X).max() <= 1e-10 * np.abs(X).max()
+        assert abs(rg["J"][i] - J) <= 1e-10 * abs(J)
