@@ -261,9 +261,29 @@ int tocreate_problem(const to_problem_desc* d, to_problem* out) {
   if (e == cudaSuccess) e = cudaMalloc(&p->d_params[1], blob32.size());
   if (e == cudaSuccess) e = cudaMemcpy(p->d_params[1], blob32.data(), blob32.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && d->actor_w) {
-    p->n_actor = d->n_actor_w;
+    // W1 b1 W2 b2 W3 b3 with every W (out x in, row-major) stored transposed
+    const int H = 256, n = d->n, m = d->m;
+    const size_t expect = (size_t)n * H + H + (size_t)H * H + H + (size_t)H * m + m;
+    if (d->n_actor_w != expect) {
+      todestroy_problem(p);
+      return fail(TO_ERR_ARG, "tocreate_problem: actor weights must be 36x256, 256, 256x256, 256, 12x256, 12");
+    }
+    std::vector<float> t(expect);
+    const float* s = d->actor_w;
+    size_t o = 0;
+    auto transpose = [&](int rows, int cols) {   // source rows x cols -> cols x rows
+      for (int i = 0; i < cols; ++i)
+        for (int j = 0; j < rows; ++j) t[o + (size_t)i * rows + j] = s[o + (size_t)j * cols + i];
+      o += (size_t)rows * cols;
+    };
+    auto copy = [&](int k) {
+      for (int i = 0; i < k; ++i) t[o + i] = s[o + i];
+      o += k;
+    };
+    transpose(H, n); copy(H); transpose(H, H); copy(H); transpose(m, H); copy(m);
+    p->n_actor = expect;
     e = cudaMalloc(&p->d_actor, p->n_actor * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_actor, d->actor_w, p->n_actor * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_actor, t.data(), p->n_actor * sizeof(float), cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
     todestroy_problem(p);

@@ -442,6 +442,47 @@ struct Solver {
     }
   }
 
+  // actor policy u = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3 (Sec. II: the
+  // actor's rollout is the TO warm start), x in w.xk, u to w.uk.  The host
+  // stores every weight matrix transposed (input-major), so lanes reading
+  // consecutive outputs of one input read consecutive words.  The hidden
+  // activations use the V A buffer, free during forward rounds.
+  static constexpr int kHidden = 256;
+  TO_DEV static void actor_mlp(const Group<G>& g, W& w, bool act, const float* aw) {
+    static_assert(!Sys::kActor || n * n >= 2 * kHidden, "hidden activations must fit the scratch buffer");
+    R* h1 = w.VA;
+    R* h2 = w.VA + kHidden;
+    const float* W1 = aw;
+    const float* b1 = W1 + n * kHidden;
+    const float* W2 = b1 + kHidden;
+    const float* b2 = W2 + kHidden * kHidden;
+    const float* W3 = b2 + kHidden;
+    const float* b3 = W3 + kHidden * m;
+    if (act)
+      for (int j = g.lane; j < kHidden; j += G) {
+        R s = (R)b1[j];
+        for (int i = 0; i < n; ++i) s += (R)W1[i * kHidden + j] * w.xk[i];
+        h1[j] = tanh(s);
+      }
+    g.sync();
+    if (act)
+      for (int j = g.lane; j < kHidden; j += G) {
+        R s = (R)b2[j];
+#pragma unroll 8
+        for (int i = 0; i < kHidden; ++i) s += (R)W2[i * kHidden + j] * h1[i];
+        h2[j] = tanh(s);
+      }
+    g.sync();
+    if (act)
+      for (int j = g.lane; j < m; j += G) {
+        R s = (R)b3[j];
+#pragma unroll 8
+        for (int i = 0; i < kHidden; ++i) s += (R)W3[i * m + j] * h2[i];
+        w.uk[j] = s;
+      }
+    g.sync();
+  }
+
   TO_DEV static R alpha_of(const SolveArgs& a, int j) {
     return sizeof(R) == sizeof(double) ? (R)a.alpha_d[j] : (R)a.alpha_f[j];
   }
@@ -556,6 +597,10 @@ struct Solver {
       {
         const bool fwd = (mode == M_NEW) || (mode == M_RUN && !release);
         const bool single = (mode == M_NEW) || forced_mode;
+        // the actor warm start runs when the problem has actor weights and no
+        // caller-given controls (uniform over the warp / CTA: it holds barriers)
+        const bool actor_rnd = Sys::kActor && a.actor_w != nullptr && a.U_init == nullptr &&
+                               !g.uniform_all(mode != M_NEW);
         const int nr = single ? 1 : (a.n_alpha + LW - 1) / LW;
         const int jforced = (mode == M_RUN && forced_mode && fwd) ? a.forced[(size_t)inst * a.max_iter + iter] : 0;
         // the trip count is the same for every group of the warp / CTA (each
@@ -588,12 +633,29 @@ struct Solver {
             if (act && nominal) store_fwd(g, w, pf);
             g.sync();
             if (act && nominal && k + 1 < T) prefetch_fwd(g, pf, rec(traj, base, k + 1, cur), gains + (base + k + 1) * GS);
+            if constexpr (Sys::kActor) {
+              // warm start from the actor policy u_k = pi(x_k): the group
+              // evaluates the MLP, lane 0 then steps the dynamics
+              if (actor_rnd) {
+                const bool run = act && mode == M_NEW;
+                if (run && g.lane == 0)
+#pragma unroll
+                  for (int i = 0; i < n; ++i) w.xk[i] = xh[i];
+                g.sync();
+                actor_mlp(g, w, run, a.actor_w);
+              }
+            }
             if (act && mine) {
               R uh[m], xn[n];
               if (mode == M_NEW) {
+                if (Sys::kActor && actor_rnd) {
 #pragma unroll
-                for (int i = 0; i < m; ++i)
-                  uh[i] = a.U_init ? (R)a.U_init[((size_t)inst * a.T_max + k) * m + i] : R(0);
+                  for (int i = 0; i < m; ++i) uh[i] = w.uk[i];
+                } else {
+#pragma unroll
+                  for (int i = 0; i < m; ++i)
+                    uh[i] = a.U_init ? (R)a.U_init[((size_t)inst * a.T_max + k) * m + i] : R(0);
+                }
               } else {
                 policy(w, alpha, xh, uh);
               }

@@ -39,7 +39,7 @@ static SysOps make_ops() {
   o.groups[0] = 64;
   o.default_G = 64;
   o.default_gpb[0] = 1; o.default_gpb[1] = 1;
-  o.accepts_actor = false;
+  o.accepts_actor = true;
   o.parse = parse_quad;
   o.launch = QDispatch::launch;
   o.occupancy = QDispatch::occupancy;

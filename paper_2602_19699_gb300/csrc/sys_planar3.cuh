@@ -42,6 +42,7 @@ inline void cast_params(const Planar3Params<S>& s, Planar3Params<D>& d) {
 
 struct SysPlanar3 {
   static constexpr int n = 6, m = 3;
+  static constexpr bool kActor = false;
   template <class R> using ParamsT = Planar3Params<R>;
 
   // absolute link angles, link and centre-of-mass vectors, joint positions

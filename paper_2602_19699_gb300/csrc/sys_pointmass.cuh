@@ -22,6 +22,7 @@ inline void cast_params(const PointMassParams<S>& s, PointMassParams<D>& d) {
 
 struct SysPointMass {
   static constexpr int n = 4, m = 2;
+  static constexpr bool kActor = false;
   template <class R> using ParamsT = PointMassParams<R>;
 
   template <class R>

@@ -100,6 +100,7 @@ template <int N_, int A0, int KIND>
 struct SysRigid {
   static constexpr int N = N_;
   static constexpr int n = 2 * N, m = N - A0;
+  static constexpr bool kActor = (KIND == RK_QUAD);   // 36 -> 256 -> 256 -> 12 actor warm start
   template <class R> using ParamsT = RigidParams<R, N>;
 
   // 3-vectors

@@ -69,14 +69,14 @@ def _errors(ro, rg, T):
     return ex, ej
 
 
-def _check(ro, rg, kappa, prec, T):
+def _check(ro, rg, kappa, prec, T, mixed_kappa=1e-14):
     if prec == "fp64":
         well = kappa < 1e-12
         xt, jt = FP64_TOL, FP64_TOL
     else:
         # float32 rounding (6e-8 per operation) is ~1e7 times the 1e-15
         # probe behind kappa: the strict bound needs kappa < 1e-14
-        well = kappa < 1e-14
+        well = kappa < mixed_kappa
         xt, jt = MIXED_X_TOL, MIXED_J_TOL
     np.testing.assert_array_equal(rg["iters"][well], ro["iters"][well])
     ex, ej = _errors(ro, rg, T)
