@@ -45,6 +45,14 @@ PLAIN_SAMPLE = 6
 L2_FLUSH_BYTES = 512 << 20
 
 
+_T_START = time.perf_counter()
+
+
+def _log(msg: str) -> None:
+    """progress on stderr (stdout carries the one JSON line)"""
+    print(f"[bench {time.perf_counter() - _T_START:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -238,6 +246,7 @@ def run_gb300(args):
         t_steps.append(e0.elapsed_time(e1) / 1e3)
     barrier()
     clk = clocks.stop()
+    _log(f"timed steps: {[round(t, 4) for t in t_steps]} s")
     launches = P.tolast_launch_count(batch) * args.steps
     t_local = float(np.sum(t_steps))
     t_max = t_local
@@ -282,6 +291,7 @@ def run_gb300(args):
         tt = torch.tensor([e2e_local], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_max = float(tt.item())
+    _log(f"e2e steps: {[round(t, 4) for t in e2e_steps]} s")
     h2d = b.x0.nbytes + b.T.astype(np.int32).nbytes
     d2h = out_X.nbytes + out_U.nbytes + out_J.nbytes + out_it.nbytes + out_st.nbytes
 
@@ -304,6 +314,7 @@ def run_gb300(args):
     r_self = oracle.Oracle.from_problem(prob).solve(x_pert, b.T[idx], max_iter=MAX_ITER, tol=TOL, n_alpha=N_ALPHA,
                                                     threads=cores)
     self_one = solved_fraction(r_self["J"], ro["J"])
+    _log(f"oracle sample of {len(idx)} done ({t_cpu:.1f} s)")
     self_two = float(np.mean(np.abs(r_self["J"] - ro["J"]) <= COST_TOL * np.abs(ro["J"])))
 
     extras = {}
@@ -343,9 +354,12 @@ def run_gb300(args):
             P.tosolve_batch_device(bp, 1, d_x0[i:i + 1].data_ptr(), d_T[i:i + 1].data_ptr(), opts=opts64, stream=sptr)
             Jp[k] = P.toget_trajectories(bp, X=False, U=False)["J"][0]
         fracp = solved_fraction(Jp, ro["J"][:PLAIN_SAMPLE])
+        _log(f"batched FP64 {t64:.2f} s; plain FP64 {len(pidx)} instances {tp:.2f} s")
         extras["plain_fp64_one_instance_per_launch"] = {
             "value": len(pidx) * fracp / tp, "raw_solves_per_s": len(pidx) / tp, "sample": len(pidx),
             "within_tol": fracp}
+
+    serve = None if args.no_extras else serve_leg(P, dev)
 
     pk, pk_src = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -398,10 +412,72 @@ def run_gb300(args):
         "clocks": clk,
     }
     line.update(extras)
+    if serve is not None:
+        line["serve"] = serve
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# serving: Poisson arrivals of single requests, continuously batched
+# --------------------------------------------------------------------------
+SERVE_RATES = {"mixed": (1e2, 1e3, 1e4, 1e5), "fp64": (1e2, 1e3)}
+SERVE_MAX_REQ = 1500
+SERVE_MAX_ITER = 30
+SERVE_BUDGET = 60 << 30
+SERVE_TIMEOUT_S = 60.0
+
+
+def serve_leg(P, dev):
+    """p50/p99 latency (from scheduled arrival to result) and solves/s per
+    arrival rate; systems point mass / planar arm / 7-DoF arm drawn uniformly,
+    T ~ U{50..400}, seeded initial states; at most SERVE_MAX_REQ requests per
+    rate (the trace lasts min(1 s, SERVE_MAX_REQ / rate))."""
+    from paper_2602_19699_gb300 import workload as W
+    systems = (W.POINTMASS, W.PLANAR3, W.ARM7)
+    probs = [W.make_problem(s, 0) for s in systems]
+    handles = [P.tocreate_problem(p.sys, p.params, 400) for p in probs]
+    out = {"workload": "Poisson arrivals; system ~ U{pointmass2d, planar3, arm7}; T ~ U{50..400}; "
+                       f"max_iter={SERVE_MAX_ITER}; HBM budget {SERVE_BUDGET >> 30} GiB; "
+                       f"<= {SERVE_MAX_REQ} requests per rate",
+           "latency": "ms from the scheduled arrival to the result (includes waiting for a seat)"}
+    for prec_name, rates in SERVE_RATES.items():
+        prec = P.TO_MIXED if prec_name == "mixed" else P.TO_FP64
+        opts = P.to_default_opts(prec=prec, max_iter=SERVE_MAX_ITER)
+        rows = []
+        for rate in rates:
+            # a fresh server per rate: a trace that does not drain in time
+            # leaves nothing behind for the next one
+            server = P.Server(handles, opts, hbm_budget_bytes=SERVE_BUDGET)
+            out["seats_" + prec_name] = server.stats()["seats"]
+            dur = min(1.0, SERVE_MAX_REQ / rate)
+            trace = W.serving_stream(rate, dur, seed=int(rate), systems=systems, T_range=(50, 400))
+            if not trace:
+                continue
+            t_arr = np.array([t for t, _, _, _ in trace])
+            pidx = np.array([systems.index(s) for _, s, _, _ in trace], np.int32)
+            Ts = np.array([T for _, _, T, _ in trace], np.int32)
+            x0 = np.zeros((len(trace), 14))
+            for i, (_, _, _, x) in enumerate(trace):
+                x0[i, :x.size] = x
+            t0 = time.perf_counter()
+            try:
+                lat, J, st = server.replay(t_arr, pidx, Ts, x0, timeout_s=SERVE_TIMEOUT_S)
+            except P.ToError as e:
+                rows.append({"rate_per_s": rate, "requests": int(len(trace)),
+                             "not_drained": f"{e} (limit {SERVE_TIMEOUT_S:.0f} s)"})
+                server.close()
+                continue
+            wall = time.perf_counter() - t0
+            rows.append({"rate_per_s": rate, "requests": int(len(trace)), "solves_per_s": len(trace) / wall,
+                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "ok_fraction": float(np.mean(np.isin(st & 15, [1, 2, 3])))})
+            server.close()
+            _log(f"serve {prec_name} rate {rate:g}: {len(trace)} requests in {wall:.2f} s")
+        out[prec_name] = rows
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -225,6 +225,46 @@ int toget_phase_cycles(to_batch b, unsigned long long* out);
 int tolast_launch_count(to_batch b);
 
 /*
+ * Serving: continuous batching of single OCP requests (the paper's real-time
+ * use, Sec. V-D).  A server holds, per problem, a pool of seats -- one
+ * instance workspace each, as many as hbm_budget_bytes (split evenly over the
+ * problems; 0 = 4 GiB) holds -- and a persistent solver kernel per problem
+ * that takes newly published requests into free seats at every iteration
+ * boundary, so requests arriving while others are on the GPU start at once
+ * and overlap with them.  Trajectories and gains stay on the device.  Every
+ * device wait is bounded: a kernel with nothing to do for ~1 ms leaves and
+ * the next tosubmit / topoll relaunches it.  opts applies to every request
+ * (forced_alpha, want_vx and profile_phases are ignored).
+ */
+typedef struct to_server_s* to_server;
+int toserver_create(const to_problem* problems, int n_problems, const to_solver_opts* opts, size_t hbm_budget_bytes,
+                    to_server* out);
+void toserver_destroy(to_server s);
+
+/* Admit one request for problems[problem] (x0: host n float64, T in
+ * [1, T_max]).  TO_ERR_BUDGET when no seat is free: poll and retry.  The
+ * request id is valid until topoll returns TO_OK for it. */
+int tosubmit(to_server s, int problem, const double* x0, int T, uint64_t* req_id);
+
+/* TO_ERR_NOTREADY while the request runs; else its results (any pointer may
+ * be NULL; X: (T_max+1) x n, U: T_max x m, padded like toget_trajectories),
+ * latency_ms = time from tosubmit to completion seen by this call, and the
+ * seat is freed. */
+int topoll(to_server s, uint64_t req_id, double* X, double* U, double* J, int* iters, int* status,
+           double* latency_ms);
+
+int toserver_stats(to_server s, int* seats_total, int* seats_busy, long long* completed, size_t* hbm_bytes);
+
+/* Replay a request trace in real time on the calling thread: request i
+ * arrives arrival_s[i] seconds after the call (sorted ascending), for
+ * problems[problem[i]] with horizon T[i] and initial state x0 + i*x0_stride.
+ * Requests wait (in arrival order) for a free seat.  latency_ms[i] is the time
+ * from the scheduled arrival to the result; J and status may be NULL.
+ * TO_ERR_TIMEOUT if the trace is not done after timeout_s seconds. */
+int toserve_replay(to_server s, int n_req, const double* arrival_s, const int* problem, const int* T,
+                   const double* x0, int x0_stride, double* latency_ms, double* J, int* status, double timeout_s);
+
+/*
  * Solve without allocating device memory.  The paper has no counterpart:
  * this is for callers that cannot call cudaMalloc while they run -- a
  * real-time control loop whose latency must stay bounded, code confined to a

@@ -27,14 +27,23 @@ _lib = None
 ST_CONVERGED, ST_MAX_ITER, ST_LS_FAIL, ST_NONFINITE, ST_FLAG_REG = 1, 2, 3, 4, 16
 
 
+# plain g++, no arch flags; no FMA contraction, so every host (x86-64 or
+# aarch64, where g++ contracts a*b+c by default) rounds each operation alike
+_FLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-pthread"]
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_lib/liboracle.so`` (plain g++, no arch flags)."""
+    """Compile the oracle into ``oracle/_lib/liboracle.so``."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    stamp = _SO + ".flags"
+    old = open(stamp).read() if os.path.exists(stamp) else ""
+    if (force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC)
+            or old != " ".join(_FLAGS)):
         tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp]
-        subprocess.run(cmd, check=True)
+        subprocess.run(["g++", *_FLAGS, _SRC, "-o", tmp], check=True)
         os.replace(tmp, _SO)
+        with open(stamp, "w") as f:
+            f.write(" ".join(_FLAGS))
     return _SO
 
 

@@ -76,6 +76,13 @@ def lib():
             L.tolast_launch_count.argtypes = [vp]
             L.toget_phase_cycles.argtypes = [vp, vp]
             L.tosolve_batch_noalloc.argtypes = [vp, i, vp, vp, C.POINTER(to_solver_opts), vp, vp, vp, vp, vp, vp]
+            L.toserver_create.argtypes = [vp, i, C.POINTER(to_solver_opts), C.c_size_t, C.POINTER(vp)]
+            L.toserver_destroy.argtypes = [vp]
+            L.toserver_destroy.restype = None
+            L.tosubmit.argtypes = [vp, i, vp, i, C.POINTER(C.c_uint64)]
+            L.topoll.argtypes = [vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
+            L.toserver_stats.argtypes = [vp, vp, vp, vp, vp]
+            L.toserve_replay.argtypes = [vp, i, vp, vp, vp, vp, i, vp, vp, vp, d]
             L.tolast_error.restype = C.c_char_p
             L.to_default_opts.argtypes = [C.POINTER(to_solver_opts)]
             L.to_default_opts.restype = None
@@ -87,7 +94,68 @@ def exported_symbols():
     return ["to_default_opts", "tocreate_problem", "todestroy_problem", "tocreate_batch", "tofree_batch",
             "tosolve_batch", "tosolve_batch_device", "toget_trajectories", "toget_history",
             "toget_device_results", "tolast_launch_count", "toget_phase_cycles", "tosolve_batch_noalloc",
+            "toserver_create", "toserver_destroy", "tosubmit", "topoll", "toserver_stats", "toserve_replay",
             "tolast_error"]
+
+
+class Server:
+    """Continuous-batching server over several problems (see include/to.h)."""
+
+    def __init__(self, problems, opts: to_solver_opts | None = None, hbm_budget_bytes: int = 0):
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.handle.value for p in self.problems])
+        self.handle = C.c_void_p()
+        _check(lib().toserver_create(arr, len(self.problems), C.byref(opts) if opts else None,
+                                     int(hbm_budget_bytes), C.byref(self.handle)))
+
+    def submit(self, problem: int, x0, T: int) -> int:
+        x = np.ascontiguousarray(x0, dtype=np.float64)
+        rid = C.c_uint64()
+        _check(lib().tosubmit(self.handle, int(problem), _ptr(x), int(T), C.byref(rid)))
+        return rid.value
+
+    def poll(self, req_id: int, problem: int | None = None, want_traj: bool = False):
+        """None while running; else dict(J, iters, status, latency_ms[, X, U])."""
+        J, it, st, lat = C.c_double(), C.c_int(), C.c_int(), C.c_double()
+        X = U = None
+        if want_traj:
+            p = self.problems[problem]
+            X = np.empty((p.T_max + 1, p.n))
+            U = np.empty((p.T_max, p.m))
+        rc = lib().topoll(self.handle, C.c_uint64(req_id), _ptr(X), _ptr(U), C.byref(J), C.byref(it), C.byref(st),
+                          C.byref(lat))
+        if rc == TO_ERR_NOTREADY:
+            return None
+        _check(rc)
+        out = {"J": J.value, "iters": it.value, "status": st.value, "latency_ms": lat.value}
+        if want_traj:
+            out["X"], out["U"] = X, U
+        return out
+
+    def stats(self):
+        tot, busy, done, nbytes = C.c_int(), C.c_int(), C.c_longlong(), C.c_size_t()
+        _check(lib().toserver_stats(self.handle, C.byref(tot), C.byref(busy), C.byref(done), C.byref(nbytes)))
+        return {"seats": tot.value, "busy": busy.value, "completed": done.value, "hbm_bytes": nbytes.value}
+
+    def replay(self, arrival_s, problem, T, x0, timeout_s: float = 600.0):
+        """Real-time replay of a request trace; returns (latency_ms, J, status)."""
+        arrival_s = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        problem = np.ascontiguousarray(problem, dtype=np.int32)
+        T = np.ascontiguousarray(T, dtype=np.int32)
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        n = arrival_s.size
+        lat, J, st = np.empty(n), np.empty(n), np.empty(n, np.int32)
+        _check(lib().toserve_replay(self.handle, n, _ptr(arrival_s), _ptr(problem), _ptr(T), _ptr(x0), x0.shape[1],
+                                    _ptr(lat), _ptr(J), _ptr(st), C.c_double(timeout_s)))
+        return lat, J, st
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.toserver_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        self.close()
 
 
 def tolast_error() -> str:

@@ -163,58 +163,7 @@ static int fail(int code, const std::string& msg) {
     if (e_ != cudaSuccess) return fail(TO_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-struct to_problem_s {
-  int sys, n, m, T_max, device;
-  const SysOps* ops;
-  std::vector<double> params;
-  void* d_params[2] = {nullptr, nullptr};   // parameter struct in float64, float32
-  float* d_actor = nullptr;
-  size_t n_actor = 0;
-};
-
-struct to_batch_s {
-  to_problem p = nullptr;
-  int B_max = 0;
-  long long knots_max = 0;
-  int elem_bytes = 0;
-  size_t bytes = 0;
-  size_t budget = 0;
-  // inputs
-  double* x0 = nullptr;
-  int* T = nullptr;
-  double* U_init = nullptr;
-  int* forced = nullptr;
-  size_t forced_cap = 0;
-  bool has_uinit = false;
-  // scheduling
-  long long* toff = nullptr;
-  int* order = nullptr;
-  int* hist = nullptr;
-  int* err = nullptr;
-  int* queue = nullptr;
-  // workspace
-  void* traj = nullptr;
-  void* gains = nullptr;
-  double* vx = nullptr;
-  // results
-  double* J = nullptr;
-  int* iters = nullptr;
-  int* status = nullptr;
-  int* slot = nullptr;
-  int* ahist = nullptr;
-  double* Jhist = nullptr;
-  int hist_iter_cap = -1;
-  // gather staging
-  double* gX = nullptr;
-  double* gU = nullptr;
-  double* gV = nullptr;
-  double* gK = nullptr;
-  unsigned long long* prof = nullptr;   // 8 per-phase cycle counters
-  // last solve
-  int B = 0, max_iter = 0, prec = TO_MIXED, want_vx = 0, launches = 0, G = 8;
-  const int* last_T = nullptr;
-  cudaStream_t stream = nullptr;
-};
+#include "handles.h"
 
 // Exported functions take C linkage from their declarations in to.h.
 
@@ -417,7 +366,7 @@ static int check_opts(const to_solver_opts* o) {
 }
 
 static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
-                        const to_solver_opts* o, cudaStream_t s) {
+                        const to_solver_opts* o, cudaStream_t s, const ServeArgs* serve = nullptr) {
   to_problem p = b->p;
   const SysOps* ops = p->ops;
   const int prec = o->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
@@ -436,7 +385,10 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   int dev = 0, sms = 0;
   TO_CK(cudaGetDevice(&dev));
   TO_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::max(1, std::min((B + gpb - 1) / gpb, bps * sms));
+  // a serving kernel takes its share of the resident blocks, so the kernels
+  // of a server's problems (one per stream) are all resident together
+  const int share = serve ? std::max(1, serve->grid_share) : 1;
+  const int grid = std::max(1, std::min((B + gpb - 1) / gpb, std::max(1, bps * sms / share)));
 
   SolveArgs a{};
   a.B = B; a.T_max = p->T_max; a.max_iter = o->max_iter; a.n_alpha = o->n_alpha;
@@ -461,9 +413,13 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
     a.prof = b->prof;
   }
 
-  prepare_kernel<<<1, 1024, 0, s>>>(B, d_T, p->T_max, b->knots_max, b->toff, b->order, b->hist, b->err, b->status,
-                                    b->queue, b->J, b->iters);
-  TO_CK(cudaGetLastError());
+  if (serve) {
+    a.serve = *serve;    // seats replace the batch; nothing to sort or offset
+  } else {
+    prepare_kernel<<<1, 1024, 0, s>>>(B, d_T, p->T_max, b->knots_max, b->toff, b->order, b->hist, b->err, b->status,
+                                      b->queue, b->J, b->iters);
+    TO_CK(cudaGetLastError());
+  }
   TO_CK(ops->launch(prec, G, gpb, grid, s, a));
   b->B = B;
   b->max_iter = o->max_iter;
@@ -474,6 +430,13 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   b->G = G;
   b->last_T = d_T;
   return TO_OK;
+}
+
+int to_fail(int code, const std::string& msg) { return fail(code, msg); }
+
+int to_launch_core(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
+                   const to_solver_opts* o, cudaStream_t s, const ServeArgs* serve) {
+  return launch_solve(b, B, d_x0, d_T, d_U, d_forced, o, s, serve);
 }
 
 int tosolve_batch_device(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U_init,

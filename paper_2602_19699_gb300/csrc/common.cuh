@@ -58,6 +58,12 @@ struct Group {
     if (kSubWarp) return __all_sync(0xffffffffu, v);
     return v;
   }
+  // the unit that shares control flow: the warp (sub-warp groups) or the CTA
+  TO_DEV bool unit_leader() const { return kSubWarp ? (threadIdx.x & 31) == 0 : lane == 0; }
+  template <class T> TO_DEV T unit_bcast(T v, T* smem_slot) const {
+    if (kSubWarp) return __shfl_sync(0xffffffffu, v, 0);
+    return bcast(v, smem_slot);
+  }
 };
 
 template <class R> TO_DEV R rsqrt_(R x);

@@ -34,7 +34,34 @@ constexpr int kMaxAlpha = 32;
 constexpr int kLsWidth = 16;                 // most step sizes tried at once
 constexpr int kMaxSlots = kLsWidth + 1;      // trajectory slots per knot for the widest groups
 
+// A serving request as published by the host in pinned, mapped memory.
+constexpr int kServeMaxN = 36;
+struct ServeDesc {
+  int seat;            // workspace seat (instance index) of the request
+  int T;               // horizon
+  unsigned seq;        // ring index + 1
+  int pad;
+  double x0[kServeMaxN];
+};
+
+// Serving mode: instead of a fixed batch, groups claim requests from a ring
+// that the host fills while the kernel runs (null ring = batch mode).
+struct ServeArgs {
+  const volatile ServeDesc* ring;   // host-mapped descriptor ring
+  int ring_size;
+  const volatile unsigned* tail;    // host-mapped: number of published requests
+  unsigned* head;                   // device: number of claimed requests
+  volatile unsigned* done;          // host-mapped, per seat: ring index + 1 when solved
+  const volatile int* stop;         // host-mapped: leave as soon as every group is idle
+  int* seat_T;                      // device, per seat: horizon of its last request
+  int* ctl;                         // device, per launch: [0] groups solving, [1] closing latch
+  volatile int* closing;            // host-mapped mirror of the latch (the host then launches anew)
+  int idle_polls;                   // polls (2 us apart) with no group solving before the kernel closes
+  int grid_share;                   // host side: the kernel gets 1/grid_share of the resident blocks
+};
+
 struct SolveArgs {
+  ServeArgs serve;
   int B, T_max, max_iter, n_alpha, refine, want_vx;
   double tol, eps;
   double alpha_d[kMaxAlpha];   // alpha_j = decay^j
@@ -516,26 +543,77 @@ struct Solver {
     int mode = M_IDLE, inst = 0, T = 0, iter = 0, status = 0, flags = 0, cur = 0;
     double J = 0;
     long long base = 0;
+    int sq = 0;          // serving: ring index of the request being solved
+    int idle = 0;        // serving: consecutive polls with every group idle
 
     while (true) {
-      // ---- refill idle groups from the queue
+      // ---- refill idle groups: the batch's queue, or the serving ring
       {
         const bool need = (mode == M_IDLE);
-        int q = 0;
-        if (need && g.lane == 0) q = atomicAdd(a.queue, 1);
+        int q = -1;
+        if (need && g.lane == 0) {
+          if (a.serve.ring) {
+            // claim the next published request, if any (never waits here)
+            // a closing launch claims nothing more; the host has launched its successor
+            if (!*reinterpret_cast<volatile int*>(a.serve.ctl + 1)) {
+              const unsigned h = *reinterpret_cast<volatile unsigned*>(a.serve.head);
+              const unsigned t = *a.serve.tail;
+              if (h < t && atomicCAS(a.serve.head, h, h + 1) == h) {
+                q = (int)h;
+                atomicAdd(a.serve.ctl, 1);
+              }
+            }
+          } else {
+            const int qq = atomicAdd(a.queue, 1);
+            q = qq < a.B ? qq : -2;
+          }
+        }
         q = g.bcast(q, &w.sel);
         if (need) {
-          if (q < a.B) {
+          if (q >= 0 && a.serve.ring) {
+            __threadfence_system();
+            const volatile ServeDesc& d = a.serve.ring[q % a.serve.ring_size];
+            inst = d.seat;
+            T = d.T;
+            base = (long long)inst * (a.T_max + 1);
+            sq = q;
+            if (g.lane == 0) a.serve.seat_T[inst] = T;
+            mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0;
+          } else if (q >= 0) {
             inst = a.order[q];
             T = a.T[inst];
             base = a.toff[inst];
             mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0;
-          } else {
+          } else if (q == -2) {
             mode = M_DRAINED;
           }
         }
       }
-      if (g.uniform_all(mode == M_DRAINED)) break;
+      if (a.serve.ring) {
+        // every group of this warp (CTA) idle: poll again after a pause.  The
+        // launch closes once no group anywhere in it has been solving for
+        // idle_polls polls: the latch stops every claim, so the whole launch
+        // drains at once and never lingers with a few warps holding it open
+        // (the host launches a successor as soon as it sees the latch)
+        if (g.uniform_all(mode == M_IDLE)) {
+          ++idle;
+          int leave = 0;
+          if (g.unit_leader()) {
+            leave = (*a.serve.stop || *reinterpret_cast<volatile int*>(a.serve.ctl + 1)) ? 1 : 0;
+            if (!leave && idle >= a.serve.idle_polls && *reinterpret_cast<volatile int*>(a.serve.ctl) == 0) {
+              atomicExch(a.serve.ctl + 1, 1);
+              *a.serve.closing = 1;
+              leave = 1;
+            }
+          }
+          if (g.unit_bcast(leave, &w.sel)) break;
+          __nanosleep(2000);
+          continue;
+        }
+        idle = 0;
+      } else if (g.uniform_all(mode == M_DRAINED)) {
+        break;
+      }
       TO_TICK(0);
       bool release = false;
       // ---- a forced sequence ends with -1
@@ -619,7 +697,8 @@ struct Solver {
           if (mine) {
             if (mode == M_NEW) {
 #pragma unroll
-              for (int i = 0; i < n; ++i) xh[i] = (R)a.x0[(size_t)inst * n + i];
+              for (int i = 0; i < n; ++i)
+                xh[i] = a.serve.ring ? (R)a.serve.ring[sq % a.serve.ring_size].x0[i] : (R)a.x0[(size_t)inst * n + i];
             } else {
               const R* r = rec(traj, base, 0, cur);
 #pragma unroll
@@ -731,6 +810,12 @@ struct Solver {
           a.iters_out[inst] = iter;
           a.status_out[inst] = status | flags;
           a.slot_out[inst] = cur;
+          if (a.serve.ring) {
+            // results first, then the completion flag the host polls
+            __threadfence_system();
+            a.serve.done[inst] = (unsigned)sq + 1u;
+            atomicSub(a.serve.ctl, 1);
+          }
         }
         mode = M_IDLE;
       }
