@@ -7,8 +7,8 @@
 //   qd+ = qd + h qdd,  q+ = q + h qd+.
 // * h(q, qd): body-frame spatial Newton-Euler (Featherstone 2008, ch. 5) with
 //   gravity as a base acceleration and the contact forces as external forces;
-// * M(q): columns from Newton-Euler at unit accelerations, zero velocity,
-//   no gravity, no contact; Cholesky-factored.
+// * M(q): composite-rigid-body algorithm (Featherstone 2008, Sec. 6.2),
+//   Cholesky-factored.
 // Derivatives: each lane propagates one tangent direction (a state
 // coordinate, or a control) through the substeps:
 //   dqdd = M^{-1} (dtau - d ID(q, qd, qdd) / d(q, qd) . (dq, dqd)),
@@ -46,6 +46,9 @@ TO_DEV float dlog1p(float a) { return log1pf(a); }
 TO_DEV double dlog1p(double a) { return log1p(a); }
 TO_DEV void dsincos(float a, float* s, float* c) { sincosf(a, s, c); }
 TO_DEV void dsincos(double a, double* s, double* c) { sincos(a, s, c); }
+TO_DEV float value_of(float a) { return a; }
+TO_DEV double value_of(double a) { return a; }
+template <class R> TO_DEV auto value_of(Dl<R> a) { return value_of(a.v); }
 template <class R> TO_DEV Dl<R> dexp(Dl<R> a) { const R e = dexp(a.v); return Dl<R>(e, e * a.d); }
 template <class R> TO_DEV Dl<R> dlog1p(Dl<R> a) { return Dl<R>(dlog1p(a.v), a.d / (R(1) + a.v)); }
 template <class R> TO_DEV void dsincos(Dl<R> a, Dl<R>* s, Dl<R>* c) {
@@ -281,10 +284,19 @@ struct SysRigid {
         for (int k = 0; k < 3; ++k) vb[k] = vv[bi][k] + wxp[k];
         mtv(E0[bi], vb, vwld);
         // normal: k softplus_beta(-z) - d sigmoid(-beta z) zdot; tangential damper
+        // softplus_beta(-z) = log(1 + exp(-beta z)) / beta and sigmoid(-beta z),
+        // evaluated with exp of a non-positive argument only (no overflow)
         const S bz = P.beta * Pw[2];
-        const S ebz = dexp(bz);
-        const S sp = (R(1) / P.beta) * dlog1p(S(R(1)) / ebz);
-        const S gate = S(R(1)) / (S(R(1)) + ebz);
+        S sp, gate;
+        if (value_of(bz) >= R(0)) {
+          const S e = dexp(-bz);
+          sp = (R(1) / P.beta) * dlog1p(e);
+          gate = e / (S(R(1)) + e);
+        } else {
+          const S e = dexp(bz);
+          sp = (R(1) / P.beta) * (dlog1p(e) - bz);
+          gate = S(R(1)) / (S(R(1)) + e);
+        }
         S F[3];
         F[0] = -(P.dc * (gate * vwld[0]));
         F[1] = -(P.dc * (gate * vwld[1]));
@@ -313,15 +325,97 @@ struct SysRigid {
     }
   }
 
-  // mass matrix columns from unit accelerations; Cholesky with reciprocal pivots
+  // Joint-space mass matrix by the composite-rigid-body algorithm
+  // (Featherstone 2008, Sec. 6.2), written into the lower triangle of L and
+  // Cholesky-factored in place with reciprocal pivots.  A subtree's composite
+  // inertia is kept about its root body's origin, in that body's coordinates,
+  // as (mass, first moment h = mass * com, rotational inertia about the
+  // origin); moving it to the parent frame rotates it and applies the
+  // parallel-axis shift.  Bodies are ordered parents first.
   template <class R>
   TO_DEV static void mass_chol(const ParamsT<R>& P, const R* q, R* L) {
-    R z[N], e[N], col[N];
-    for (int i = 0; i < N; ++i) z[i] = R(0);
-    for (int j = 0; j < N; ++j) {
-      for (int i = 0; i < N; ++i) e[i] = (i == j) ? R(1) : R(0);
-      rnea<R, R>(P, q, z, e, false, false, col);
-      for (int i = j; i < N; ++i) L[i * N + j] = col[i];
+    R E[N][9], r[N][3];
+    R cm[N], ch[N][3], cI[N][6];   // cI: xx, yy, zz, xy, xz, yz
+    for (int i = 0; i < N; ++i) {
+      joint_transform(P, i, q[i], E[i], r[i]);
+      const R mi = P.mass[i], c0 = P.com[i][0], c1 = P.com[i][1], c2 = P.com[i][2];
+      cm[i] = mi;
+      ch[i][0] = mi * c0; ch[i][1] = mi * c1; ch[i][2] = mi * c2;
+      // I_origin = I_com + m (|c|^2 1 - c c^T)
+      cI[i][0] = P.inertia[i][0] + mi * (c1 * c1 + c2 * c2);
+      cI[i][1] = P.inertia[i][1] + mi * (c0 * c0 + c2 * c2);
+      cI[i][2] = P.inertia[i][2] + mi * (c0 * c0 + c1 * c1);
+      cI[i][3] = -mi * c0 * c1; cI[i][4] = -mi * c0 * c2; cI[i][5] = -mi * c1 * c2;
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      const int pa = P.parent[i];
+      if (pa < 0) continue;
+      const R* e = E[i];
+      const R* rr = r[i];
+      const R mi = cm[i];
+      // h_A = E^T h (parent coordinates, about the child origin)
+      R hA[3];
+      mtv(e, ch[i], hA);
+      // I_A = E^T I E
+      const R I3[9] = {cI[i][0], cI[i][3], cI[i][4], cI[i][3], cI[i][1], cI[i][5], cI[i][4], cI[i][5], cI[i][2]};
+      R T[9];   // I E
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) T[a * 3 + b] = I3[a * 3 + 0] * e[0 * 3 + b] + I3[a * 3 + 1] * e[1 * 3 + b] + I3[a * 3 + 2] * e[2 * 3 + b];
+      R IA[6];
+      const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        IA[k] = e[0 * 3 + ia[k]] * T[0 * 3 + ib[k]] + e[1 * 3 + ia[k]] * T[1 * 3 + ib[k]] + e[2 * 3 + ia[k]] * T[2 * 3 + ib[k]];
+      // shift to the parent origin (child origin at r):
+      // I_O = I_A + m (|r|^2 1 - r r^T) + 2 (r.h_A) 1 - (h_A r^T + r h_A^T)
+      const R r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+      const R rh = rr[0] * hA[0] + rr[1] * hA[1] + rr[2] * hA[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cI[pa][k] += IA[k] + mi * (r2 - rr[k] * rr[k]) + R(2) * (rh - hA[k] * rr[k]);
+#pragma unroll
+      for (int k = 3; k < 6; ++k) cI[pa][k] += IA[k] - mi * rr[ia[k]] * rr[ib[k]] - (hA[ia[k]] * rr[ib[k]] + rr[ia[k]] * hA[ib[k]]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ch[pa][k] += hA[k] + mi * rr[k];
+      cm[pa] += mi;
+    }
+    // entries of bodies on different branches stay zero
+    for (int i = 0; i < N * N; ++i) L[i] = R(0);
+    for (int i = 0; i < N; ++i) {
+      // F = Ic_i S_i: revolute about axis a: (I e_a, e_a x h); prismatic along a: (h x e_a, m e_a)
+      R fn[3], ff[3];
+      const int jt = P.jtype[i];
+      const R* c6 = cI[i];
+      if (jt <= 2) {
+        const int a = jt;
+        const int col[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+        fn[0] = c6[col[0][a]]; fn[1] = c6[col[1][a]]; fn[2] = c6[col[2][a]];
+        R ea[3] = {R(0), R(0), R(0)};
+        ea[a] = R(1);
+        cross(ea, ch[i], ff);
+      } else {
+        const int a = jt - 3;
+        R ea[3] = {R(0), R(0), R(0)};
+        ea[a] = R(1);
+        cross(ch[i], ea, fn);
+        ff[0] = R(0); ff[1] = R(0); ff[2] = R(0);
+        ff[a] = cm[i];
+      }
+      L[i * N + i] = jt <= 2 ? fn[jt] : ff[jt - 3];
+      int j = i;
+      while (P.parent[j] >= 0) {
+        // force to the parent frame: f_p = E^T f, n_p = E^T n + r x f_p
+        R en[3], ef[3], rf[3];
+        mtv(E[j], fn, en);
+        mtv(E[j], ff, ef);
+        cross(r[j], ef, rf);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { fn[k] = en[k] + rf[k]; ff[k] = ef[k]; }
+        j = P.parent[j];
+        const int jj = P.jtype[j];
+        L[i * N + j] = jj <= 2 ? fn[jj] : ff[jj - 3];
+      }
     }
     for (int j = 0; j < N; ++j) {
       R s = L[j * N + j];

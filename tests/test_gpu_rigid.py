@@ -35,18 +35,22 @@ def _solver(P, prob, T_max, prec, actor=False):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_arm7_replay(P, oracle_mod, prec):
     prob = W.arm7(seed=1)
-    b = W.make_batch(prob, 8, seed=3, T=(20, 60))
+    if prec == "fp64":
+        b = W.make_batch(prob, 8, seed=3, T=(20, 60))
+        iters = 12
+    else:
+        # float32 needs well-conditioned replays: short horizons, few
+        # iterations (the chain's own rounding noise under the 1e-15 probe is
+        # already ~1e-14, so only the best-conditioned instances take the
+        # strict bound; the rest take the conditioning-scaled one)
+        b = W.make_batch(prob, 16, seed=3, T=(10, 20))
+        iters = 3
     o = oracle_mod.Oracle.from_problem(prob)
-    iters = 12 if prec == "fp64" else 3      # float32 needs a well-conditioned (short) replay
     ro = o.solve(b.x0, b.T, max_iter=iters, tol=1e-8)
     kappa = _sensitivity(o, b, ro, iters)
     s = _solver(P, prob, 64, P.TO_FP64 if prec == "fp64" else P.TO_MIXED)
     rg = s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=iters)
-    # the chain's own rounding noise under the 1e-15 probe is ~1e-14; float32
-    # rounding (6e-8) amplified by kappa/1e-15 stays below 1e-4 for kappa
-    # under ~2.5e-13 (one instance at 2.7e-13 reached 1.35e-4); the others go
-    # through the ill-conditioned bound
-    well = _check(ro, rg, kappa, prec, b.T, mixed_kappa=2.5e-13)
+    well = _check(ro, rg, kappa, prec, b.T)
     assert well.sum() >= 2
     _check_consistency(o, b, rg, prec, min_checked=4)
 
