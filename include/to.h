@@ -154,8 +154,13 @@ typedef struct {
                              gives V_x and the gains K, k there                */
   size_t hbm_budget_bytes;/* 0 = no limit; else tocreate_batch / tosolve_batch
                              refuse a workspace larger than this (TO_ERR_BUDGET) */
-  int group_lanes;        /* threads per instance (4..256); 0 = autotuned       */
-  int groups_per_block;   /* instances resident per CTA; 0 = autotuned          */
+  int group_lanes;        /* threads per instance, one of the system's supported
+                             sizes (8/16/32 planar systems, 32 arm, 64
+                             quadruped); 0 = the totune choice, else the
+                             system's default                                 */
+  int groups_per_block;   /* instances resident per CTA (group_lanes x
+                             groups_per_block <= 256, a multiple of 32);
+                             0 = the totune choice, else the default          */
   int profile_phases;     /* 1: accumulate per-phase clock64 cycles (tracing;
                              see toget_phase_cycles); 0 = off                 */
 } to_solver_opts;
@@ -291,6 +296,62 @@ int toserve_replay(to_server s, int n_req, const double* arrival_s, const int* p
 #define TO_NOALLOC_SCRATCH_BYTES (64u << 20)
 int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_T, const to_solver_opts* opts,
                           void* cuda_stream, double* d_J, int* d_iters, int* d_status, double* d_X, double* d_U);
+
+/*
+ * Launch-shape autotuner.  The solver kernel's shape -- threads per instance
+ * (group_lanes, from the system's supported set) and instances per CTA
+ * (groups_per_block) -- trades per-instance parallelism against occupancy
+ * and register pressure, and the best point differs per system and
+ * precision.  totune times every valid shape on a calibration batch (host
+ * x0: B x n, T: B; solved with *opts, whose max_iter may be smaller than the
+ * production one) with CUDA events on a stream of its own, after one untimed
+ * warm-up solve per shape.  The fastest shape is written into
+ * opts->group_lanes / groups_per_block and cached in the problem for
+ * opts->prec: later solves that leave both at 0 use it.  rows (may be NULL)
+ * receives up to max_rows measured shapes; *n_rows how many were measured.
+ * The calibration batch should fill the GPU (several instances per SM) so
+ * the choice holds for large batches.  Errors: TO_ERR_ARG, TO_ERR_CUDA.
+ */
+typedef struct {
+  int group_lanes, groups_per_block;
+  int grid;               /* CTAs launched                                     */
+  int ctas_per_sm;        /* resident CTAs per SM at this shape                */
+  double ms;              /* device time of one solve of the calibration batch */
+} to_tune_row;
+int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* opts, to_tune_row* rows,
+           int max_rows, int* n_rows);
+
+/*
+ * CUDA-graph solves of a multi-system batch.  One graph replays the whole
+ * solve of n member batches (one per problem, member i solving B[i]
+ * instances): per member, the host-to-device copies of x0 and T from pinned
+ * staging that the graph owns, the horizon sort, the persistent solver
+ * kernel, the gather of X and U (when want_traj) and the device-to-host
+ * copies of X, U, J, iters and status into pinned staging.  The members'
+ * branches are independent, so their kernels run at the same time, each
+ * sized to its share of the resident CTAs (shares[i] / sum(shares); shares
+ * NULL = equal).  Horizons may change between launches (the sort runs on the
+ * device); B, the options and the member batches are fixed at capture.
+ * opts may not set forced_alpha, want_vx or profile_phases
+ * (TO_ERR_UNSUPPORTED).  The member batches must outlive the graph and must
+ * not be used by other solves while a launch is in flight.
+ */
+typedef struct to_graph_s* to_graph;
+int tograph_create(const to_batch* batches, const int* B, const double* shares, int n, const to_solver_opts* opts,
+                   int want_traj, to_graph* out);
+/* Pinned staging of member i: inputs to fill before tograph_launch (x0:
+ * B x n, T: B) and outputs valid after tograph_sync (X: B x (T_max+1) x n and
+ * U: B x T_max x m, NULL without want_traj; J, iters, status: B).  Any output
+ * pointer argument may be NULL. */
+int tograph_staging(to_graph g, int member, double** x0, int** T, double** X, double** U, double** J, int** iters,
+                    int** status);
+/* Enqueue one replay on cuda_stream (NULL = the graph's own stream). */
+int tograph_launch(to_graph g, void* cuda_stream);
+/* Wait for the last replay. */
+int tograph_sync(to_graph g);
+/* Kernels one replay launches. */
+int tograph_launch_count(to_graph g);
+void tograph_destroy(to_graph g);
 
 const char* tolast_error(void);
 

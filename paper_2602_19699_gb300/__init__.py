@@ -83,6 +83,14 @@ def lib():
             L.topoll.argtypes = [vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
             L.toserver_stats.argtypes = [vp, vp, vp, vp, vp]
             L.toserve_replay.argtypes = [vp, i, vp, vp, vp, vp, i, vp, vp, vp, d]
+            L.totune.argtypes = [vp, i, vp, vp, C.POINTER(to_solver_opts), vp, i, vp]
+            L.tograph_create.argtypes = [vp, vp, vp, i, C.POINTER(to_solver_opts), i, C.POINTER(vp)]
+            L.tograph_staging.argtypes = [vp, i] + [C.POINTER(vp)] * 7
+            L.tograph_launch.argtypes = [vp, vp]
+            L.tograph_sync.argtypes = [vp]
+            L.tograph_launch_count.argtypes = [vp]
+            L.tograph_destroy.argtypes = [vp]
+            L.tograph_destroy.restype = None
             L.tolast_error.restype = C.c_char_p
             L.to_default_opts.argtypes = [C.POINTER(to_solver_opts)]
             L.to_default_opts.restype = None
@@ -95,7 +103,91 @@ def exported_symbols():
             "tosolve_batch", "tosolve_batch_device", "toget_trajectories", "toget_history",
             "toget_device_results", "tolast_launch_count", "toget_phase_cycles", "tosolve_batch_noalloc",
             "toserver_create", "toserver_destroy", "tosubmit", "topoll", "toserver_stats", "toserve_replay",
-            "tolast_error"]
+            "totune", "tograph_create", "tograph_staging", "tograph_launch", "tograph_sync", "tograph_launch_count",
+            "tograph_destroy", "tolast_error"]
+
+
+class to_tune_row(C.Structure):
+    _fields_ = [("group_lanes", C.c_int), ("groups_per_block", C.c_int), ("grid", C.c_int),
+                ("ctas_per_sm", C.c_int), ("ms", C.c_double)]
+
+
+def totune(problem: "Problem", x0, T, opts: "to_solver_opts", max_rows: int = 64):
+    """Time every valid launch shape on the calibration batch (x0, T); the
+    fastest is written into ``opts`` and cached in the problem.  Returns the
+    measured rows as dicts."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    rows = (to_tune_row * max_rows)()
+    n = C.c_int()
+    _check(lib().totune(problem.handle, int(T.size), _ptr(x0), _ptr(T), C.byref(opts), rows, max_rows, C.byref(n)))
+    return [{"group_lanes": r.group_lanes, "groups_per_block": r.groups_per_block, "grid": r.grid,
+             "ctas_per_sm": r.ctas_per_sm, "ms": r.ms} for r in rows[:n.value]]
+
+
+class Graph:
+    """A captured multi-system solve (one member batch per problem).  Fill
+    ``inputs(i)`` (pinned x0, T views), ``launch()``, ``sync()``, read
+    ``outputs(i)`` (pinned views, valid until the next launch)."""
+
+    def __init__(self, batches, B, opts: "to_solver_opts | None" = None, shares=None, want_traj: bool = True):
+        self.batches = list(batches)
+        self.B = [int(b) for b in B]
+        hb = (C.c_void_p * len(self.batches))(*[b.handle.value for b in self.batches])
+        Bs = (C.c_int * len(self.B))(*self.B)
+        sh = None if shares is None else (C.c_double * len(shares))(*[float(x) for x in shares])
+        self.handle = C.c_void_p()
+        self.want_traj = bool(want_traj)
+        _check(lib().tograph_create(hb, Bs, sh, len(self.batches), C.byref(opts) if opts else None,
+                                    int(self.want_traj), C.byref(self.handle)))
+        self._views = [self._member_views(i) for i in range(len(self.batches))]
+        for bt, Bi in zip(self.batches, self.B):
+            bt.B = Bi
+            bt.max_iter = opts.max_iter if opts else 100
+
+    def _member_views(self, i):
+        ptrs = [C.c_void_p() for _ in range(7)]
+        _check(lib().tograph_staging(self.handle, i, *[C.byref(p) for p in ptrs]))
+        prob = self.batches[i].problem
+        B = self.B[i]
+
+        def view(p, shape, ctype, dtype):
+            if not p.value:
+                return None
+            n = int(np.prod(shape))
+            return np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(n,)).view(dtype).reshape(shape)
+        return {"x0": view(ptrs[0], (B, prob.n), C.c_double, np.float64),
+                "T": view(ptrs[1], (B,), C.c_int, np.int32),
+                "X": view(ptrs[2], (B, prob.T_max + 1, prob.n), C.c_double, np.float64),
+                "U": view(ptrs[3], (B, prob.T_max, prob.m), C.c_double, np.float64),
+                "J": view(ptrs[4], (B,), C.c_double, np.float64),
+                "iters": view(ptrs[5], (B,), C.c_int, np.int32),
+                "status": view(ptrs[6], (B,), C.c_int, np.int32)}
+
+    def inputs(self, i):
+        v = self._views[i]
+        return v["x0"], v["T"]
+
+    def outputs(self, i):
+        v = self._views[i]
+        return {k: v[k] for k in ("X", "U", "J", "iters", "status")}
+
+    def launch(self, stream=None):
+        _check(lib().tograph_launch(self.handle, stream))
+
+    def sync(self):
+        _check(lib().tograph_sync(self.handle))
+
+    def launch_count(self) -> int:
+        return lib().tograph_launch_count(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.tograph_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        self.close()
 
 
 class Server:

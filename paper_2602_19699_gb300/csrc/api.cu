@@ -365,19 +365,25 @@ static int check_opts(const to_solver_opts* o) {
   return TO_OK;
 }
 
-static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
-                        const to_solver_opts* o, cudaStream_t s, const ServeArgs* serve = nullptr) {
-  to_problem p = b->p;
+// launch shape of a solve: group size, groups per CTA, CTAs (persistent:
+// at most frac of the CTAs the GPU holds resident at once)
+static int resolve_shape(to_problem p, const to_solver_opts* o, int B, double frac, int* G_out, int* gpb_out,
+                         int* grid_out, int* bps_out) {
   const SysOps* ops = p->ops;
   const int prec = o->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
-  int G = o->group_lanes ? o->group_lanes : ops->default_G;
-  int gpb = o->groups_per_block ? o->groups_per_block : ops->default_gpb[prec];
+  int G = o->group_lanes, gpb = o->groups_per_block;
+  if (!G && !gpb && p->tuned_G[prec]) {
+    G = p->tuned_G[prec];
+    gpb = p->tuned_gpb[prec];
+  }
+  if (!G) G = ops->default_G;
+  if (!gpb) gpb = ops->default_gpb[prec];
   bool okG = false;
   for (int i = 0; i < ops->n_groups; ++i) okG |= ops->groups[i] == G;
   if (!okG) return fail(TO_ERR_ARG, "opts: group_lanes not supported by this system");
   if (G <= 32 && (G * gpb) % 32 != 0) return fail(TO_ERR_ARG, "opts: groups_per_block * group_lanes must be a multiple of 32");
   if (G > 32 && gpb != 1) return fail(TO_ERR_ARG, "opts: groups_per_block must be 1 when group_lanes > 32");
-  if (G * gpb > 1024) return fail(TO_ERR_ARG, "opts: CTA larger than 1024 threads");
+  if (G * gpb > kMaxCtaThreads) return fail(TO_ERR_ARG, "opts: CTA larger than 256 threads");
   size_t smem = 0;
   int bps = 0;
   TO_CK(ops->occupancy(prec, G, gpb, &smem, &bps));
@@ -385,10 +391,25 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   int dev = 0, sms = 0;
   TO_CK(cudaGetDevice(&dev));
   TO_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // a serving kernel takes its share of the resident blocks, so the kernels
-  // of a server's problems (one per stream) are all resident together
-  const int share = serve ? std::max(1, serve->grid_share) : 1;
-  const int grid = std::max(1, std::min((B + gpb - 1) / gpb, std::max(1, bps * sms / share)));
+  const int cap = std::max(1, (int)(bps * sms * std::min(1.0, std::max(frac, 0.0))));
+  *G_out = G;
+  *gpb_out = gpb;
+  *grid_out = std::max(1, std::min((B + gpb - 1) / gpb, cap));
+  if (bps_out) *bps_out = bps;
+  return TO_OK;
+}
+
+static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
+                        const to_solver_opts* o, cudaStream_t s, const ServeArgs* serve = nullptr) {
+  to_problem p = b->p;
+  const SysOps* ops = p->ops;
+  const int prec = o->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
+  // a serving kernel, or a member of a multi-system graph, takes its share of
+  // the resident CTAs, so the kernels of the other problems run beside it
+  const double frac = serve ? 1.0 / std::max(1, serve->grid_share) : b->grid_frac;
+  int G = 0, gpb = 0, grid = 0;
+  int rc = resolve_shape(p, o, B, frac, &G, &gpb, &grid, nullptr);
+  if (rc) return rc;
 
   SolveArgs a{};
   a.B = B; a.T_max = p->T_max; a.max_iter = o->max_iter; a.n_alpha = o->n_alpha;
@@ -433,6 +454,32 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
 }
 
 int to_fail(int code, const std::string& msg) { return fail(code, msg); }
+
+int to_check_opts(const to_solver_opts* o) { return check_opts(o); }
+
+int to_resolve_shape(to_problem p, const to_solver_opts* o, int B, double frac, int* G, int* gpb, int* grid, int* bps) {
+  return resolve_shape(p, o, B, frac, G, gpb, grid, bps);
+}
+
+int to_ensure_workspace(to_batch b, const to_solver_opts* o, bool want_traj) {
+  int rc = ensure_options(b, o, false, false);
+  if (rc) return rc;
+  to_problem p = b->p;
+  size_t dummy = 0;
+  if (want_traj && !b->gX) TO_CK(grow(b->gX, (size_t)b->B_max * (p->T_max + 1) * p->n, dummy));
+  if (want_traj && !b->gU) TO_CK(grow(b->gU, (size_t)b->B_max * p->T_max * p->m, dummy));
+  return TO_OK;
+}
+
+int to_enqueue_gather(to_batch b, int B, const int* d_T, double* d_X, double* d_U, cudaStream_t s) {
+  to_problem p = b->p;
+  const int pi = b->prec == TO_FP64 ? 0 : 1;
+  const int NS = std::min(b->G, kLsWidth) + 1;
+  gather_kernel<<<1024, 256, 0, s>>>(B, p->T_max, p->n, p->m, p->ops->rs[pi], p->ops->gs[pi], NS, pi == 0 ? 8 : 4,
+                                     b->toff, d_T, b->slot, b->traj, b->gains, nullptr, d_X, d_U, nullptr, nullptr);
+  TO_CK(cudaGetLastError());
+  return TO_OK;
+}
 
 int to_launch_core(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
                    const to_solver_opts* o, cudaStream_t s, const ServeArgs* serve) {

@@ -16,6 +16,8 @@ struct to_problem_s {
   void* d_params[2] = {nullptr, nullptr};   // parameter struct in float64, float32
   float* d_actor = nullptr;
   size_t n_actor = 0;
+  int tuned_G[2] = {0, 0};     // autotuned launch shape per precision (FP64, mixed); 0 = none
+  int tuned_gpb[2] = {0, 0};
 };
 
 struct to_batch_s {
@@ -60,6 +62,7 @@ struct to_batch_s {
   int B = 0, max_iter = 0, prec = TO_MIXED, want_vx = 0, launches = 0, G = 8;
   const int* last_T = nullptr;
   cudaStream_t stream = nullptr;
+  double grid_frac = 1.0;      // share of the resident CTAs a solve of this batch may take
 };
 
 // record the calling thread's error message and return code
@@ -69,3 +72,18 @@ int to_fail(int code, const std::string& msg);
 // solver claims requests from the serving ring and no prepare kernel runs)
 int to_launch_core(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
                    const to_solver_opts* o, cudaStream_t s, const to::ServeArgs* serve);
+
+// option validation (TO_ERR_ARG on a bad value)
+int to_check_opts(const to_solver_opts* o);
+
+// launch shape of a solve of B instances allowed frac of the resident CTAs
+int to_resolve_shape(to_problem p, const to_solver_opts* o, int B, double frac, int* G, int* gpb, int* grid,
+                     int* ctas_per_sm);
+
+// grow the option-dependent workspace (per-iteration history; with
+// want_traj, the X / U gather staging) so that a solve allocates nothing
+int to_ensure_workspace(to_batch b, const to_solver_opts* o, bool want_traj);
+
+// gather the last solve's X (B x (T_max+1) x n) and U (B x T_max x m) as
+// float64 into device buffers (either may be null) on stream s
+int to_enqueue_gather(to_batch b, int B, const int* d_T, double* d_X, double* d_U, cudaStream_t s);

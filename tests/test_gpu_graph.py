@@ -1,0 +1,99 @@
+"""CUDA-graph solves of a multi-system batch and the launch-shape autotuner.
+
+* a captured graph of three systems (point mass, planar arm, 7-DoF arm; each
+  its own branch and persistent kernel) gives, per member, the same results
+  as that member solved alone with tosolve_batch, and new inputs written into
+  the staging between replays (other initial states, other horizons) are
+  picked up;
+* the launch shape changes the schedule, not the arithmetic: solves at every
+  supported shape agree;
+* totune measures every valid shape, returns the fastest, and later solves
+  with an unset shape use it.
+"""
+import numpy as np
+import pytest
+
+from paper_2602_19699_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2602_19699_gb300 as P
+    P.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return P
+
+
+def _alone(P, handle, x0, T, opts):
+    bt = P.tosolve_batch(handle, x0, T, opts=opts)
+    return P.toget_trajectories(bt)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_members_equal_separate_solves(P, prec):
+    T_max = 120
+    probs = [W.pointmass(seed=1), W.planar3(seed=2), W.arm7(seed=3)]
+    Bs = [96, 160, 40]
+    handles = [P.tocreate_problem(p.sys, p.params, T_max) for p in probs]
+    opts = P.to_default_opts(prec=P.TO_FP64 if prec == "fp64" else P.TO_MIXED, max_iter=8)
+    batches = [P.tocreate_batch(h, B, B * (T_max + 1), opts) for h, B in zip(handles, Bs)]
+    g = P.Graph(batches, Bs, opts=opts, shares=[1.0, 2.0, 2.0])
+    assert g.launch_count() == 9
+    for rnd in range(2):
+        data = []
+        for i, (p, B) in enumerate(zip(probs, Bs)):
+            b = W.make_batch(p, B, seed=10 * rnd + i, T=(30, T_max) if rnd == 0 else (5, 60))
+            x0s, Ts = g.inputs(i)
+            x0s[:] = b.x0
+            Ts[:] = b.T
+            data.append(b)
+        g.launch()
+        g.sync()
+        for i, (h, b) in enumerate(zip(handles, data)):
+            out = g.outputs(i)
+            ref = _alone(P, h, b.x0, b.T, opts)
+            np.testing.assert_array_equal(out["iters"], ref["iters"])
+            np.testing.assert_array_equal(out["status"], ref["status"])
+            np.testing.assert_array_equal(out["J"], ref["J"])
+            np.testing.assert_array_equal(out["X"], ref["X"])
+            np.testing.assert_array_equal(out["U"], ref["U"])
+    g.close()
+
+
+def test_launch_shape_does_not_change_results(P):
+    prob = W.planar3(seed=4)
+    b = W.make_batch(prob, 200, seed=5, T=(20, 80))
+    h = P.tocreate_problem(prob.sys, prob.params, 80)
+    ref = None
+    for G, gpb in [(8, 4), (8, 8), (16, 2), (16, 8), (32, 1), (32, 4)]:
+        opts = P.to_default_opts(prec=P.TO_FP64, max_iter=6, group_lanes=G, groups_per_block=gpb)
+        r = _alone(P, h, b.x0, b.T, opts)
+        if ref is None:
+            ref = r
+            continue
+        np.testing.assert_array_equal(r["iters"], ref["iters"])
+        np.testing.assert_array_equal(r["J"], ref["J"])
+        np.testing.assert_array_equal(r["X"], ref["X"])
+
+
+def test_totune_picks_the_fastest_and_caches_it(P):
+    prob = W.planar3(seed=6)
+    b = W.make_batch(prob, 2048, seed=7, T=(50, 150))
+    h = P.tocreate_problem(prob.sys, prob.params, 150)
+    opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=3)
+    rows = P.totune(h, b.x0, b.T, opts)
+    assert len(rows) >= 6                      # 3 group sizes x several CTA shapes
+    best = min(rows, key=lambda r: r["ms"])
+    assert (opts.group_lanes, opts.groups_per_block) == (best["group_lanes"], best["groups_per_block"])
+    for r in rows:
+        assert r["ms"] > 0 and r["ctas_per_sm"] >= 1
+        assert r["group_lanes"] * r["groups_per_block"] <= 256
+    # an unset shape now means the tuned one; the results equal an explicit solve at that shape
+    o0 = P.to_default_opts(prec=P.TO_MIXED, max_iter=3)
+    bt = P.tosolve_batch(h, b.x0[:256], b.T[:256], opts=o0)
+    r0 = P.toget_trajectories(bt, X=False, U=False)
+    r1 = _alone(P, h, b.x0[:256], b.T[:256], opts)
+    np.testing.assert_array_equal(r0["J"], r1["J"])
