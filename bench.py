@@ -161,12 +161,15 @@ def fp32_alu_peak_tflops(sm_mhz: float, sms: int) -> float:
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+# the sources the timed planar-arm solver kernel is compiled from
+KERNEL_SOURCES = ("common.cuh", "ilqr.cuh", "launch.cuh", "sys_planar3.cuh", "solve_planar3.cu")
+
+
 def kernel_sources_digest() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_19699_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -209,7 +212,14 @@ def run_gb300(args):
     knots = int(np.sum(b.T + 1))
     problem = P.tocreate_problem(prob.sys, prob.params, T_MAX)
     opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=MAX_ITER, tol_rel=TOL, n_alpha=N_ALPHA)
-    batch = P.tocreate_batch(problem, B, knots, opts)
+    # launch shape: the autotuner on the workload itself, 3 iterations per
+    # calibration solve (excluded from timing, like a JIT warm-up)
+    tune_opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=3, tol_rel=TOL, n_alpha=N_ALPHA)
+    tune_rows = P.totune(problem, b.x0, b.T, tune_opts)
+    opts.group_lanes, opts.groups_per_block = tune_opts.group_lanes, tune_opts.groups_per_block
+    _log(f"autotune: G={opts.group_lanes} x {opts.groups_per_block} per CTA "
+         f"({len(tune_rows)} shapes, {min(r['ms'] for r in tune_rows):.1f} .. {max(r['ms'] for r in tune_rows):.1f} ms)")
+    batch = P.tocreate_batch(problem, B, B * (T_MAX + 1), opts)
     dev = torch.device("cuda", local)
     d_x0 = torch.tensor(b.x0, dtype=torch.float64, device=dev)
     d_T = torch.tensor(b.T, dtype=torch.int32, device=dev)
@@ -259,22 +269,21 @@ def run_gb300(args):
     J_g = P.toget_trajectories(batch, X=False, U=False)
     ah, _ = P.toget_history(batch)
     alg = flops.solve_flops(prob.sys, prob.n, prob.m, b.T, J_g["iters"], J_g["status"], ah,
-                            lanes_per_round=8, n_alpha=N_ALPHA, refine=True)
+                            lanes_per_round=min(opts.group_lanes, 16), n_alpha=N_ALPHA, refine=True)
 
-    # ---- e2e: host buffers through the public API, copies inside the region
-    pin_x0 = torch.tensor(b.x0, dtype=torch.float64).pin_memory().numpy()
-    pin_T = torch.tensor(b.T, dtype=torch.int32).pin_memory().numpy()
-    out_X = torch.empty((B, T_MAX + 1, prob.n), dtype=torch.float64).pin_memory().numpy()
-    out_U = torch.empty((B, T_MAX, prob.m), dtype=torch.float64).pin_memory().numpy()
-    out_J = torch.empty(B, dtype=torch.float64).pin_memory().numpy()
-    out_it = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
-    out_st = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
+    # ---- e2e: the public graph API.  Each step writes the inputs into the
+    # graph's pinned staging and replays the captured solve: host-to-device
+    # copies, horizon sort, solver, gather, device-to-host copies of X, U, J,
+    # iters and status, all inside the timed region.
+    graph = P.Graph([batch], [B], opts=opts, want_traj=True)
+    gx0, gT = graph.inputs(0)
+
     def solve_e2e():
-        P.tosolve_batch(problem, pin_x0, pin_T, opts=opts, stream=sptr, batch=batch)
-        rc = P.lib().toget_trajectories(batch.handle, P._ptr(out_X), P._ptr(out_U), P._ptr(out_J), P._ptr(out_it),
-                                        P._ptr(out_st), None, None)
-        if rc != 0:
-            raise RuntimeError(P.tolast_error())
+        gx0[:] = b.x0
+        gT[:] = b.T
+        graph.launch(sptr)
+        graph.sync()
+        return graph.outputs(0)
 
     solve_e2e()
     barrier()
@@ -283,7 +292,7 @@ def run_gb300(args):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        solve_e2e()
+        out_e2e = solve_e2e()
         e2e_steps.append(time.perf_counter() - ts)
     e2e_local = float(np.sum(e2e_steps))
     e2e_max = e2e_local
@@ -291,9 +300,11 @@ def run_gb300(args):
         tt = torch.tensor([e2e_local], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_max = float(tt.item())
-    _log(f"e2e steps: {[round(t, 4) for t in e2e_steps]} s")
+    _log(f"e2e steps (graph replay): {[round(t, 4) for t in e2e_steps]} s")
     h2d = b.x0.nbytes + b.T.astype(np.int32).nbytes
-    d2h = out_X.nbytes + out_U.nbytes + out_J.nbytes + out_it.nbytes + out_st.nbytes
+    d2h = sum(out_e2e[k].nbytes for k in ("X", "U", "J", "iters", "status"))
+    e2e_launches = graph.launch_count()
+    e2e_same = bool(np.array_equal(out_e2e["J"], J_g["J"]))   # graph replay == device-resident solve
 
     if rank != 0:
         if ws > 1:
@@ -365,6 +376,8 @@ def run_gb300(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     peak32 = fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0), sms)
+    peak64 = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0), sms)
+    others = None if args.no_extras else config_legs(P, dev, flush, peak32, peak64)
     achieved = alg / (t_local / args.steps) / 1e12
     traffic = measured_traffic()
     n = ws
@@ -390,7 +403,8 @@ def run_gb300(args):
                         f"max_iter={MAX_ITER}, tol={TOL}, {N_ALPHA} step sizes",
             "batch_per_gpu": B, "knots_per_gpu": knots, "parallelism": f"independent instances x{n}",
             "l2": "flushed between steps (512 MB write); working set ~1.7 GB > L2",
-            "launch": "persistent kernel, 8 lanes per instance, 8 instances per CTA",
+            "launch": f"persistent kernel, {opts.group_lanes} lanes per instance, {opts.groups_per_block} "
+                      f"instances per CTA (autotuned)",
         },
         "raw_solves_per_s": n * B / t_step,
         "within_tol": {"cost_tol": COST_TOL, "sample": int(len(idx)), "fraction": frac_mixed,
@@ -399,7 +413,12 @@ def run_gb300(args):
                        "oracle_self_reproducibility": {"one_sided": self_one, "two_sided": self_two,
                                                        "perturbation": "x0 * (1 +- 1e-15)"}},
         "e2e": {"value": n * B * frac_mixed / (e2e_max / args.steps), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_max / args.steps * 1e3,
+                "api": "tograph_launch of a captured solve (H2D from pinned staging, sort, solver, gather, D2H)",
+                "kernels_per_step": int(e2e_launches), "results_equal_device_solve": e2e_same},
+        "autotune": {"chosen": [int(opts.group_lanes), int(opts.groups_per_block)],
+                     "calibration": "the workload itself, max_iter=3",
+                     "rows": [[r["group_lanes"], r["groups_per_block"], round(r["ms"], 2)] for r in tune_rows]},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                      "frac": achieved / peak32, "traffic": traffic,
@@ -414,6 +433,8 @@ def run_gb300(args):
     line.update(extras)
     if serve is not None:
         line["serve"] = serve
+    if others is not None:
+        line["other_workloads"] = others
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
@@ -477,6 +498,118 @@ def serve_leg(P, dev):
             server.close()
             _log(f"serve {prec_name} rate {rate:g}: {len(trace)} requests in {wall:.2f} s")
         out[prec_name] = rows
+    return out
+
+
+# --------------------------------------------------------------------------
+# the other synthetic workloads: point mass (FP64, latency-bound), 7-DoF arm
+# (precision comparison), quadruped-shaped base (actor warm start, mixed)
+# --------------------------------------------------------------------------
+CONFIGS = {
+    "pointmass": dict(B=64, T=50, max_iter=100, precs=("fp64",), oracle_sample=64, fp64_subset=None),
+    "arm7": dict(B=16384, T=200, max_iter=10, precs=("mixed", "fp64"), oracle_sample=32, fp64_subset=2048),
+    "quad": dict(B=2048, T=100, max_iter=5, precs=("mixed", "fp64"), oracle_sample=0, fp64_subset=32),
+}
+
+
+def fp64_alu_peak_tflops(sm_mhz: float, sms: int) -> float:
+    """152 SMs x 2 FP64 lanes x 2 FLOP per FMA x SM clock (1/64 of the FP32 rate)."""
+    return sms * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _timed_solve(P, batch, B, d_x0, d_T, opts, stream, flush, reps):
+    import torch
+    P.tosolve_batch_device(batch, B, d_x0.data_ptr(), d_T.data_ptr(), opts=opts, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.tosolve_batch_device(batch, B, d_x0.data_ptr(), d_T.data_ptr(), opts=opts, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.median(ts))
+
+
+def config_legs(P, dev, flush, peak32, peak64):
+    import torch
+    from paper_2602_19699_gb300 import flops
+    from paper_2602_19699_gb300 import workload as W
+    import oracle
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, c in CONFIGS.items():
+        sysid = {"pointmass": W.POINTMASS, "arm7": W.ARM7, "quad": W.QUAD}[name]
+        prob = W.make_problem(sysid, 0)
+        actor = prob.actor_w if sysid == W.QUAD else None
+        b = W.make_batch(prob, c["B"], seed=0, T=c["T"])
+        problem = P.tocreate_problem(prob.sys, prob.params, c["T"], actor_w=actor)
+        d_x0 = torch.tensor(b.x0, dtype=torch.float64, device=dev)
+        d_T = torch.tensor(b.T, dtype=torch.int32, device=dev)
+        row = {"workload": f"{name}: B={c['B']}, T={c['T']}, max_iter={c['max_iter']}, tol={TOL}, "
+                           f"{N_ALPHA} step sizes" + (", actor warm start" if actor is not None else ", zero warm start")}
+        res = {}
+        for prec_name in c["precs"]:
+            prec = P.TO_MIXED if prec_name == "mixed" else P.TO_FP64
+            B = c["B"] if (prec_name == "mixed" or not c["fp64_subset"]) else c["fp64_subset"]
+            opts = P.to_default_opts(prec=prec, max_iter=c["max_iter"], tol_rel=TOL, n_alpha=N_ALPHA)
+            batch = P.tocreate_batch(problem, B, B * (c["T"] + 1), opts)
+            reps = 3 if name == "pointmass" else 1
+            t = _timed_solve(P, batch, B, d_x0[:B], d_T[:B], opts, stream, flush, reps)
+            r = P.toget_trajectories(batch, X=True, U=True)
+            ah, _ = P.toget_history(batch)
+            lanes = {W.POINTMASS: 8, W.ARM7: 16, W.QUAD: 16}[sysid]
+            alg = flops.solve_flops(prob.sys, prob.n, prob.m, b.T[:B], r["iters"], r["status"], ah,
+                                    lanes_per_round=lanes, n_alpha=N_ALPHA, refine=prec == P.TO_MIXED,
+                                    params=prob.params, actor=actor is not None)
+            peak = peak32 if prec == P.TO_MIXED else peak64
+            achieved = alg / t / 1e12
+            bound = "latency" if name == "pointmass" else "alu"
+            res[prec_name] = {"B": B, "ms": t * 1e3, "raw_solves_per_s": B / t,
+                              "us_per_iteration": t / max(float(np.max(r["iters"])), 1) * 1e6,
+                              "mean_iters": float(np.mean(r["iters"])),
+                              "status_counts": np.bincount(r["status"] & 15, minlength=6)[1:].tolist(),
+                              "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                           "frac": achieved / peak, "algorithmic_flops": alg,
+                                           "peak_source": "derived " + ("FP32" if prec == P.TO_MIXED else "FP64")
+                                                          + " ALU rate at the max SM clock",
+                                           "note": ("64 instances of 50 knots: a dependent chain per instance on a "
+                                                    "nearly idle GPU; the fraction is not meaningful, the time per "
+                                                    "iteration is") if name == "pointmass" else ""},
+                              "_J": r["J"], "_X": r["X"]}
+            _log(f"config {name} {prec_name}: B={B} {t * 1e3:.1f} ms, mean iters {np.mean(r['iters']):.1f}")
+        # accuracy: against the FP64 oracle on a sample, or (quadruped, whose
+        # oracle takes minutes per instance) against the GPU's FP64 mode,
+        # which the parity tests tie to the oracle
+        ns = c["oracle_sample"]
+        if ns:
+            o = oracle.Oracle.from_problem(prob)
+            idx = np.arange(ns)
+            ro = o.solve(b.x0[idx], b.T[idx], max_iter=c["max_iter"], tol=TOL, n_alpha=N_ALPHA,
+                         threads=os.cpu_count() or 1)
+            Jref, Xref, ref_name = ro["J"], ro["X"], "FP64 CPU oracle"
+        else:
+            idx = np.arange(c["fp64_subset"])
+            Jref, Xref, ref_name = res["fp64"]["_J"][idx], res["fp64"]["_X"][idx], "GPU FP64 mode"
+        for prec_name, rr in res.items():
+            if prec_name == "fp64" and ref_name == "GPU FP64 mode":
+                continue
+            J = rr["_J"][idx]
+            X = rr["_X"][idx]
+            rel = np.abs(J - Jref) / np.abs(Jref)
+            xe = np.array([np.abs(X[i] - Xref[i]).max() / max(np.abs(Xref[i]).max(), 1e-300) for i in range(len(idx))])
+            frac = solved_fraction(J, Jref)
+            rr["accuracy"] = {"reference": ref_name, "sample": int(len(idx)), "within_cost_tol_one_sided": frac,
+                              "cost_rel_err_median": float(np.median(rel)), "cost_rel_err_max": float(np.max(rel)),
+                              "traj_rel_err_median": float(np.median(xe)), "traj_rel_err_max": float(np.max(xe))}
+            rr["value"] = rr["raw_solves_per_s"] * frac
+        for rr in res.values():
+            rr.pop("_J")
+            rr.pop("_X")
+        row.update(res)
+        out[name] = row
     return out
 
 

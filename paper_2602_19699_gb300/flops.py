@@ -18,6 +18,22 @@ cos and exp count 1 each) of the minimal formulation of each step, per knot:
 The per-system constants below are hand counts of those formulations (the
 planar arm: world-frame Newton-Euler 111, closed-form CRBA 106, 3x3 Cholesky
 12, solve 18, kinematics 27).
+
+Rigid-body trees (7-DoF arm, quadruped) are counted from their joint tree
+(N bodies, parents first) with n_sub semi-implicit Euler substeps per knot;
+per substep:
+
+* Newton-Euler, per body, with single-axis joints: velocity 25, acceleration
+  27, body force (two inertia products and three cross products) 96, force
+  back to the parent 27, joint transform 2 -> 177; the quadruped adds the
+  world pose of every body (60) and the four feet's contact forces (80 each);
+* composite-rigid-body mass matrix: 70 per non-root body (rotate and shift
+  the composite inertia), 10 per body (F = I_c S), 24 per (body, ancestor)
+  pair (one force transform);
+* dense Cholesky N^3 / 3, two triangular solves 2 N^2, integration 4 N;
+* one tangent direction (a state coordinate or a control) carried through
+  the substep: twice the Newton-Euler work (product rule) plus the solve and
+  the integration.
 """
 from __future__ import annotations
 
@@ -43,25 +59,55 @@ _SYSTEM = {
 }
 
 
-def derivative_flops(sys: int, n: int, m: int) -> int:
+ACTOR_FLOPS_PER_KNOT = 2 * (36 * 256 + 256 * 256 + 256 * 12) + 2 * 256   # 36-256-256-12 MLP, tanh
+
+
+def rigid_counts(params) -> dict:
+    """Per-knot FLOPs of a rigid-body tree from its parameter vector."""
+    p = np.asarray(params, dtype=np.float64)
+    N, n_sub = int(p[4]), max(int(p[6]), 1)
+    parent = [int(p[8 + 16 * i]) for i in range(N)]
+    depth = []
+    for i in range(N):
+        depth.append(0 if parent[i] < 0 else depth[parent[i]] + 1)
+    pairs = sum(depth)
+    roots = sum(1 for x in parent if x < 0)
+    quad = N == 18
+    rnea = 177 * N + (60 * N + 80 * 4 if quad else 0)
+    crba = 70 * (N - roots) + 10 * N + 24 * pairs
+    solve = 2 * N * N
+    primal_sub = rnea + crba + N ** 3 // 3 + solve + 4 * N
+    tangent_sub = 2 * rnea + solve + 4 * N
+    return dict(N=N, n_sub=n_sub, primal=n_sub * primal_sub, tangent=n_sub * tangent_sub, costd=8 * N,
+                cost=6 * N)
+
+
+def derivative_flops(sys: int, n: int, m: int, params=None) -> int:
+    if sys in (ARM7, QUAD):
+        c = rigid_counts(params)
+        return c["primal"] + (n + m) * c["tangent"] + c["costd"]
     c = _SYSTEM[sys]
     if sys == POINTMASS:
         return c["costd"]
     return c["primal"] + n * c["tangent"] + m * c["minv"] + c["costd"]
 
 
-def rollout_flops(sys: int, n: int, m: int) -> int:
+def rollout_flops(sys: int, n: int, m: int, params=None) -> int:
+    if sys in (ARM7, QUAD):
+        c = rigid_counts(params)
+        return 2 * m * n + 3 * m + n + c["primal"] + c["cost"]
     return 2 * m * n + 3 * m + n + _SYSTEM[sys]["cost_step"]
 
 
 def solve_flops(sys: int, n: int, m: int, T: np.ndarray, iters: np.ndarray, status: np.ndarray,
-                alpha_hist: np.ndarray, lanes_per_round: int, n_alpha: int, refine: bool) -> float:
+                alpha_hist: np.ndarray, lanes_per_round: int, n_alpha: int, refine: bool, params=None,
+                actor: bool = False) -> float:
     """Algorithmic FLOPs of one batched solve from its per-instance history."""
     T = np.asarray(T, dtype=np.float64)
     iters = np.asarray(iters)
-    bwd = riccati_flops(n, m, refine) + derivative_flops(sys, n, m)
-    ro = rollout_flops(sys, n, m)
-    total = float(np.sum(T) * ro)                       # warm-start rollout
+    bwd = riccati_flops(n, m, refine) + derivative_flops(sys, n, m, params)
+    ro = rollout_flops(sys, n, m, params)
+    total = float(np.sum(T) * (ro + (ACTOR_FLOPS_PER_KNOT if actor else 0)))   # warm-start rollout
     total += float(np.sum(T * iters) * bwd)             # one backward pass per iteration
     # candidates evaluated: lanes_per_round per round; an accepted index j
     # needs j // lanes_per_round + 1 rounds; a failed search runs every round
