@@ -70,6 +70,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest of the ranks' values (every rank gets it); the tensor lives
+    on ``device`` (the GPU under NCCL, the CPU under gloo)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, seconds_max: float, ws: int) -> float:
+    """Whole-job rate under weak scaling: every rank solves its own batch of
+    the same size, so the job's units are ws x units_per_rank, done when the
+    slowest rank is."""
+    return ws * units_per_rank / seconds_max
+
+
 def workload(rank: int):
     from paper_2602_19699_gb300 import workload as W
     prob = W.planar3(seed=0)
@@ -259,11 +277,7 @@ def run_gb300(args):
     _log(f"timed steps: {[round(t, 4) for t in t_steps]} s")
     launches = P.tolast_launch_count(batch) * args.steps
     t_local = float(np.sum(t_steps))
-    t_max = t_local
-    if ws > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_local, ws, dev)
 
     # results of the last timed step
     J_g = P.toget_trajectories(batch, X=False, U=False)
@@ -295,11 +309,7 @@ def run_gb300(args):
         out_e2e = solve_e2e()
         e2e_steps.append(time.perf_counter() - ts)
     e2e_local = float(np.sum(e2e_steps))
-    e2e_max = e2e_local
-    if ws > 1:
-        tt = torch.tensor([e2e_local], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_max = float(tt.item())
+    e2e_max = max_over_ranks(e2e_local, ws, dev)
     _log(f"e2e steps (graph replay): {[round(t, 4) for t in e2e_steps]} s")
     h2d = b.x0.nbytes + b.T.astype(np.int32).nbytes
     d2h = sum(out_e2e[k].nbytes for k in ("X", "U", "J", "iters", "status"))
@@ -382,7 +392,7 @@ def run_gb300(args):
     traffic = measured_traffic()
     n = ws
     t_step = t_max / args.steps
-    value = n * B * frac_mixed / t_step
+    value = job_throughput(B * frac_mixed, t_step, n)
     line = {
         "metric": METRIC,
         "value": value,
@@ -406,13 +416,13 @@ def run_gb300(args):
             "launch": f"persistent kernel, {opts.group_lanes} lanes per instance, {opts.groups_per_block} "
                       f"instances per CTA (autotuned)",
         },
-        "raw_solves_per_s": n * B / t_step,
+        "raw_solves_per_s": job_throughput(B, t_step, n),
         "within_tol": {"cost_tol": COST_TOL, "sample": int(len(idx)), "fraction": frac_mixed,
                        "rule": "final J <= (1 + 1e-6) * J of the FP64 CPU oracle on the same instance",
                        "two_sided_fraction": two_sided,
                        "oracle_self_reproducibility": {"one_sided": self_one, "two_sided": self_two,
                                                        "perturbation": "x0 * (1 +- 1e-15)"}},
-        "e2e": {"value": n * B * frac_mixed / (e2e_max / args.steps), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": job_throughput(B * frac_mixed, e2e_max / args.steps, n), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_max / args.steps * 1e3,
                 "api": "tograph_launch of a captured solve (H2D from pinned staging, sort, solver, gather, D2H)",
                 "kernels_per_step": int(e2e_launches), "results_equal_device_solve": e2e_same},
