@@ -130,8 +130,8 @@ __global__ void gather_kernel(int B, int T_max, int n, int m, int RS, int GS, in
     auto rd = [&](const void* p, long long idx) -> double {
       return rbytes == 8 ? reinterpret_cast<const double*>(p)[idx] : (double)reinterpret_cast<const float*>(p)[idx];
     };
-    if (X)
-      for (int i = 0; i < n; ++i) X[t * n + i] = rd(traj, xr + i);
+    if (X)   // float32 records carry the state's low parts after u
+      for (int i = 0; i < n; ++i) X[t * n + i] = rd(traj, xr + i) + (rbytes == 4 ? rd(traj, xr + n + m + i) : 0.0);
     if (U && k < T_max)
       for (int i = 0; i < m; ++i)
         U[((long long)b * T_max + k) * m + i] = k < Tb ? rd(traj, ((base + k) * NS + sl) * RS + n + i) : 0.0;

@@ -66,16 +66,183 @@ struct Group {
   }
 };
 
+// State accumulation (hi, lo) += d.  In float32 the pair carries the state
+// to about 48 bits (two-sum, then renormalised so |lo| <= ulp(hi) / 2), so a
+// long rollout loses no more than the increments' own rounding; in float64
+// it is the plain sum (lo stays 0).
+template <class R>
+TO_DEV void acc2(R& hi, R& lo, R d) {
+  if constexpr (sizeof(R) == 4) {
+    const R s = hi + d;
+    const R bv = s - hi;
+    const R e = (hi - (s - bv)) + (d - bv);
+    const R l = lo + e;
+    hi = s + l;
+    lo = l - (hi - s);
+  } else {
+    hi += d;
+  }
+}
+
+// one semi-implicit Euler step of (q, v) carried as (hi, lo) pairs:
+// v+ = v + h a,  q+ = q + h v+
+template <class R, int N>
+TO_DEV void semi_implicit2(R* qh, R* ql, R* vh, R* vl, const R* a, R h) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    acc2(vh[i], vl[i], h * a[i]);
+    acc2(qh[i], ql[i], h * vh[i] + h * vl[i]);
+  }
+}
+
 template <class R> TO_DEV R rsqrt_(R x);
 template <> TO_DEV float rsqrt_(float x) { return rsqrtf(x); }
 template <> TO_DEV double rsqrt_(double x) { return rsqrt(x); }
 
 TO_DEV bool finite_d(double x) { return isfinite(x); }
 
-// In-place cyclic Jacobi eigen-decomposition of a small symmetric matrix
-// (Golub & Van Loan sec. 8.5) followed by eigenvalue clipping
-//   S' = max(S, eps),  Q_psd = sym(W diag(S') W^T)        (Sec. IV-B)
-// One thread; P is row-major P x P.
+// Unit eigenvector of the symmetric 3x3 A for the eigenvalue lam: the largest
+// cross product of two rows of A - lam I (they span the orthogonal complement
+// when lam is simple).
+template <class R>
+TO_DEV void eigvec_sym3(const R* A, R lam, R* w) {
+  const R r0[3] = {A[0] - lam, A[1], A[2]}, r1[3] = {A[3], A[4] - lam, A[5]}, r2[3] = {A[6], A[7], A[8] - lam};
+  R c[3][3];
+  const R* ra[3] = {r0, r0, r1};
+  const R* rb[3] = {r1, r2, r2};
+  R best = R(-1);
+  int bi = 0;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    c[t][0] = ra[t][1] * rb[t][2] - ra[t][2] * rb[t][1];
+    c[t][1] = ra[t][2] * rb[t][0] - ra[t][0] * rb[t][2];
+    c[t][2] = ra[t][0] * rb[t][1] - ra[t][1] * rb[t][0];
+    const R nn = c[t][0] * c[t][0] + c[t][1] * c[t][1] + c[t][2] * c[t][2];
+    if (nn > best) { best = nn; bi = t; }
+  }
+  const R inv = best > R(0) ? rsqrt_(best) : R(0);
+  w[0] = c[bi][0] * inv; w[1] = c[bi][1] * inv; w[2] = c[bi][2] * inv;
+}
+
+// Clip of a symmetric 2x2 [a b; b c]: one Jacobi rotation diagonalises it
+// exactly (Golub & Van Loan sec. 8.5.2); the rotation is scale-free, so tiny
+// entries (far from a bump, in float32) cannot underflow into 0/0.
+template <class R>
+TO_DEV void eigclip_2x2(R& a, R& b, R& c, R eps) {
+  if (b == R(0)) {
+    a = a > eps ? a : eps;
+    c = c > eps ? c : eps;
+    return;
+  }
+  const R tau = (c - a) / (R(2) * b);
+  const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+  const R cs = rsqrt_(R(1) + t * t), sn = t * cs;
+  R d1 = a - t * b, d2 = c + t * b;     // eigenvalues
+  d1 = d1 > eps ? d1 : eps;
+  d2 = d2 > eps ? d2 : eps;
+  // [a b; b c] = J diag(d1, d2) J^T with J = [cs sn; -sn cs]
+  a = cs * cs * d1 + sn * sn * d2;
+  c = sn * sn * d1 + cs * cs * d2;
+  b = cs * sn * (d2 - d1);
+}
+
+// Eigenvalue clip of a symmetric 3x3 without iteration.  The eigenvalue that
+// is farthest from the other two comes from the characteristic cubic in
+// trigonometric form (Smith, CACM 4(4), 1961) -- the largest when the cubic's
+// angle puts the close pair below, else the smallest; unlike the close pair
+// it is well conditioned there -- and its eigenvector from a cross product
+// of two rows of Q - lam I.  The rest is the exact 2x2 problem on the
+// orthogonal complement (one Jacobi rotation).  Q' = max(lam, eps) w w^T
+// + U clip(U^T Q U) U^T.
+template <class R>
+TO_DEV void eigclip_sym3(R* Qio, R eps_in) {
+  // work on Q / max|Q_ij| (the clip commutes with positive scaling), so that
+  // products of tiny entries cannot underflow
+  R mx = R(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) mx = fabs(Qio[i]) > mx ? fabs(Qio[i]) : mx;
+  if (!(mx > R(0))) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Qio[i] = (i % 4 == 0) ? (eps_in > R(0) ? eps_in : R(0)) : R(0);
+    return;
+  }
+  const R sc = R(1) / mx;
+  R Q[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Q[i] = Qio[i] * sc;
+  const R eps = eps_in * sc;
+  const R a00 = Q[0], a11 = Q[4], a22 = Q[8], a01 = Q[1], a02 = Q[2], a12 = Q[5];
+  const R p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  if (p1 == R(0)) {
+    Qio[0] = (a00 > eps ? a00 : eps) * mx;
+    Qio[4] = (a11 > eps ? a11 : eps) * mx;
+    Qio[8] = (a22 > eps ? a22 : eps) * mx;
+    return;
+  }
+  const R q = (a00 + a11 + a22) * R(1.0 / 3.0);
+  const R b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+  const R p = sqrt((b00 * b00 + b11 * b11 + b22 * b22 + R(2) * p1) * R(1.0 / 6.0));
+  const R ip = R(1) / p;
+  const R c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+  R r = R(0.5) * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02));
+  r = r < R(-1) ? R(-1) : (r > R(1) ? R(1) : r);
+  const R phi = acos(r) * R(1.0 / 3.0);
+  const R lam = r >= R(0) ? q + R(2) * p * cos(phi) : q + R(2) * p * cos(phi + R(2.0943951023931954923));
+  R w[3];
+  eigvec_sym3(Q, lam, w);
+  // orthonormal basis (u1, u2) of the complement of w
+  const R aw0 = fabs(w[0]), aw1 = fabs(w[1]), aw2 = fabs(w[2]);
+  const int k = (aw0 <= aw1 && aw0 <= aw2) ? 0 : (aw1 <= aw2 ? 1 : 2);
+  R u1[3];   // w x e_k
+  u1[0] = k == 0 ? R(0) : (k == 1 ? -w[2] : w[1]);
+  u1[1] = k == 0 ? w[2] : (k == 1 ? R(0) : -w[0]);
+  u1[2] = k == 0 ? -w[1] : (k == 1 ? w[0] : R(0));
+  const R n1 = rsqrt_(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+  u1[0] *= n1; u1[1] *= n1; u1[2] *= n1;
+  const R u2[3] = {w[1] * u1[2] - w[2] * u1[1], w[2] * u1[0] - w[0] * u1[2], w[0] * u1[1] - w[1] * u1[0]};
+  R Qu1[3], Qu2[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Qu1[i] = Q[i * 3] * u1[0] + Q[i * 3 + 1] * u1[1] + Q[i * 3 + 2] * u1[2];
+    Qu2[i] = Q[i * 3] * u2[0] + Q[i * 3 + 1] * u2[1] + Q[i * 3 + 2] * u2[2];
+  }
+  const R e11 = u1[0] * Qu1[0] + u1[1] * Qu1[1] + u1[2] * Qu1[2];
+  const R e12 = u1[0] * Qu2[0] + u1[1] * Qu2[1] + u1[2] * Qu2[2];
+  const R e22 = u2[0] * Qu2[0] + u2[1] * Qu2[1] + u2[2] * Qu2[2];
+  // the clip as a correction to Q (exact zero where nothing is clipped):
+  // dl along w, and the 2x2 block's eigen-corrections rotated back
+  const R dl = lam < eps ? eps - lam : R(0);
+  R f11, f12, f22;
+  if (e12 == R(0)) {
+    f11 = e11 < eps ? eps - e11 : R(0);
+    f22 = e22 < eps ? eps - e22 : R(0);
+    f12 = R(0);
+  } else {
+    const R tau = (e22 - e11) / (R(2) * e12);
+    const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+    const R cs = rsqrt_(R(1) + t * t), sn = t * cs;
+    const R d1 = e11 - t * e12, d2 = e22 + t * e12;
+    const R g1 = d1 < eps ? eps - d1 : R(0), g2 = d2 < eps ? eps - d2 : R(0);
+    f11 = cs * cs * g1 + sn * sn * g2;
+    f22 = sn * sn * g1 + cs * cs * g2;
+    f12 = cs * sn * (g2 - g1);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const R v = Qio[i * 3 + j] + (dl * w[i] * w[j] + f11 * u1[i] * u1[j] + f12 * (u1[i] * u2[j] + u2[i] * u1[j]) +
+                                    f22 * u2[i] * u2[j]) * mx;
+      Qio[i * 3 + j] = v;
+      Qio[j * 3 + i] = v;
+    }
+}
+
+// Eigenvalue clipping of a small symmetric matrix (Sec. IV-B),
+//   S' = max(S, eps),  Q_psd = sym(W diag(S') W^T),
+// after two exact shortcuts; 3x3 blocks then take the closed form above,
+// larger ones an in-place cyclic Jacobi eigen-decomposition (Golub & Van
+// Loan sec. 8.5).  One thread; P is row-major P x P.
 template <class R, int P>
 TO_DEV void eigclip_small(R* Q, R eps) {
   // Two exact shortcuts before the iteration:
@@ -118,6 +285,10 @@ TO_DEV void eigclip_small(R* Q, R eps) {
       C[j][j] = s * r;
     }
     if (pd) return;
+  }
+  if constexpr (P == 3) {
+    eigclip_sym3(Q, eps);
+    return;
   }
   R A[P][P], W[P][P];
 #pragma unroll
@@ -254,28 +425,6 @@ TO_DEV void eigclip_jacobi(R* Q, R eps) {
       Q[i * P + j] = s;
       Q[j * P + i] = s;
     }
-}
-
-// Clip of a symmetric 2x2 [a b; b c]: one Jacobi rotation diagonalises it
-// exactly (Golub & Van Loan sec. 8.5.2); the rotation is scale-free, so tiny
-// entries (far from a bump, in float32) cannot underflow into 0/0.
-template <class R>
-TO_DEV void eigclip_2x2(R& a, R& b, R& c, R eps) {
-  if (b == R(0)) {
-    a = a > eps ? a : eps;
-    c = c > eps ? c : eps;
-    return;
-  }
-  const R tau = (c - a) / (R(2) * b);
-  const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
-  const R cs = rsqrt_(R(1) + t * t), sn = t * cs;
-  R d1 = a - t * b, d2 = c + t * b;     // eigenvalues
-  d1 = d1 > eps ? d1 : eps;
-  d2 = d2 > eps ? d2 : eps;
-  // [a b; b c] = J diag(d1, d2) J^T with J = [cs sn; -sn cs]
-  a = cs * cs * d1 + sn * sn * d2;
-  c = sn * sn * d1 + cs * cs * d2;
-  b = cs * sn * (d2 - d1);
 }
 
 }  // namespace to

@@ -96,11 +96,15 @@ struct SolveArgs {
     tlast = t_;                                                                      \
   }
 
+// knot record [x | u | x_lo | pad]: in float32 the state's low parts ride
+// along (the rollouts carry the state as (hi, lo) pairs, acc2); gain record
+// [K | k | pad]; both padded to 16 bytes
 template <class Sys, class R>
 struct Layout {
   static constexpr int n = Sys::n, m = Sys::m;
   static constexpr int kVec = 16 / (int)sizeof(R);
-  static constexpr int RS = (n + m + kVec - 1) / kVec * kVec;
+  static constexpr int kLo = sizeof(R) == 4 ? n : 0;
+  static constexpr int RS = (n + m + kLo + kVec - 1) / kVec * kVec;
   static constexpr int GS = (m * (n + 1) + kVec - 1) / kVec * kVec;
 };
 
@@ -147,6 +151,7 @@ struct Work {
   R luu[m * m];
   R xk[n];               // staged knot record: x_k, u_k (adjacent)
   R uk[m];
+  R xl[n];               // low parts of x_k (float32 rollouts)
   R K[m * n];            // gains K_k, k_k (adjacent)
   R kf[m];
   int flag;              // Cholesky: 0 ok, 1 regularised, 2 failed
@@ -160,7 +165,8 @@ template <class Sys, class R, int G>
 struct Solver {
   static constexpr int n = Sys::n, m = Sys::m;
   static constexpr int RS = Layout<Sys, R>::RS, GS = Layout<Sys, R>::GS;
-  static constexpr int NF = n + m + m * (n + 1);          // forward record: x, u, K, k
+  static constexpr int kLo = Layout<Sys, R>::kLo;
+  static constexpr int NF = n + m + m * (n + 1) + kLo;    // forward record: x, u, K, k, x_lo
   static constexpr int PF = (NF + G - 1) / G;             // prefetch registers per lane (forward)
   static constexpr int PB = (n + m + G - 1) / G;          // prefetch registers per lane (backward)
   static constexpr int LW = G < kLsWidth ? G : kLsWidth;   // step sizes per line-search round
@@ -435,9 +441,10 @@ struct Solver {
     return flag;
   }
 
-  // forward record (x_k, u_k, K_k, k_k) element e of the lane's prefetch slot
+  // forward record (x_k, u_k, K_k, k_k, x_lo) element e of the lane's prefetch slot
   TO_DEV static R load_fwd(const R* trec, const R* grec, int e) {
-    return e < n + m ? trec[e] : grec[e - (n + m)];
+    constexpr int NG = m * (n + 1);
+    return e < n + m ? trec[e] : (e < n + m + NG ? grec[e - (n + m)] : trec[e - NG]);
   }
   TO_DEV static void prefetch_fwd(const Group<G>& g, R (&pf)[PF], const R* trec, const R* grec) {
 #pragma unroll
@@ -451,15 +458,16 @@ struct Solver {
     for (int s = 0; s < PF; ++s) {
       const int e = g.lane + s * G;
       if (e < n + m) w.xk[e] = pf[s];
-      else if (e < NF) w.K[e - (n + m)] = pf[s];
+      else if (e < n + m + m * (n + 1)) w.K[e - (n + m)] = pf[s];
+      else if (e < NF) w.xl[e - (n + m + m * (n + 1))] = pf[s];
     }
   }
 
-  // u^ = u + alpha k + K (x^ - x)
-  TO_DEV static void policy(const W& w, R alpha, const R* xh, R* uh) {
+  // u^ = u + alpha k + K (x^ - x), the difference taken on (hi, lo) pairs
+  TO_DEV static void policy(const W& w, R alpha, const R* xh, const R* xlo, R* uh) {
     R dx[n];
 #pragma unroll
-    for (int j = 0; j < n; ++j) dx[j] = xh[j] - w.xk[j];
+    for (int j = 0; j < n; ++j) dx[j] = kLo ? (xh[j] - w.xk[j]) + (xlo[j] - w.xl[j]) : xh[j] - w.xk[j];
 #pragma unroll
     for (int i = 0; i < m; ++i) {
       R s = w.uk[i] + alpha * w.kf[i];
@@ -691,18 +699,24 @@ struct Solver {
           const int slot = (mode == M_NEW) ? 0 : (g.lane < cur ? g.lane : g.lane + 1);
           const R alpha = alpha_of(a, (j >= 0 && j < kMaxAlpha) ? j : 0);
           const bool nominal = need && mode != M_NEW;   // needs the current iterate and gains
-          R xh[n];
+          R xh[n], xlo[n];   // the candidate's state as (hi, lo) pairs (lo = 0 in float64)
           Acc<R> Jc;
           R pf[PF];
           if (mine) {
             if (mode == M_NEW) {
 #pragma unroll
-              for (int i = 0; i < n; ++i)
-                xh[i] = a.serve.ring ? (R)a.serve.ring[sq % a.serve.ring_size].x0[i] : (R)a.x0[(size_t)inst * n + i];
+              for (int i = 0; i < n; ++i) {
+                const double x0 = a.serve.ring ? a.serve.ring[sq % a.serve.ring_size].x0[i] : a.x0[(size_t)inst * n + i];
+                xh[i] = (R)x0;
+                xlo[i] = kLo ? (R)(x0 - (double)xh[i]) : R(0);
+              }
             } else {
               const R* r = rec(traj, base, 0, cur);
 #pragma unroll
-              for (int i = 0; i < n; ++i) xh[i] = r[i];
+              for (int i = 0; i < n; ++i) {
+                xh[i] = r[i];
+                xlo[i] = kLo ? r[n + m + i] : R(0);
+              }
             }
           }
           if (nominal) prefetch_fwd(g, pf, rec(traj, base, 0, cur), gains + base * GS);
@@ -725,7 +739,7 @@ struct Solver {
               }
             }
             if (act && mine) {
-              R uh[m], xn[n];
+              R uh[m];
               if (mode == M_NEW) {
                 if (Sys::kActor && actor_rnd) {
 #pragma unroll
@@ -736,16 +750,17 @@ struct Solver {
                     uh[i] = a.U_init ? (R)a.U_init[((size_t)inst * a.T_max + k) * m + i] : R(0);
                 }
               } else {
-                policy(w, alpha, xh, uh);
+                policy(w, alpha, xh, xlo, uh);
               }
               R* r = rec(traj, base, k, slot);
 #pragma unroll
               for (int i = 0; i < n; ++i) r[i] = xh[i];
 #pragma unroll
               for (int i = 0; i < m; ++i) r[n + i] = uh[i];
-              Jc.add(Sys::cost_step(P, xh, uh, xn));
+              if (kLo)
 #pragma unroll
-              for (int i = 0; i < n; ++i) xh[i] = xn[i];
+                for (int i = 0; i < n; ++i) r[n + m + i] = xlo[i];
+              Jc.add(Sys::cost_step2(P, xh, xlo, uh));
             }
             g.sync();
           }
@@ -755,6 +770,9 @@ struct Solver {
             R* r = rec(traj, base, T, slot);
 #pragma unroll
             for (int i = 0; i < n; ++i) r[i] = xh[i];
+            if (kLo)
+#pragma unroll
+              for (int i = 0; i < n; ++i) r[n + m + i] = xlo[i];
             Jc.add(Sys::terminal_cost(P, xh));
             Jt = Jc.value();
             if (single || Jt < J) best = single ? 0 : j;   // strict decrease, compared in float64

@@ -263,6 +263,23 @@ struct SysPlanar3 {
     return l;
   }
 
+  // the same step on a state carried as (hi, lo) pairs, in place
+  template <class R>
+  TO_DEV static R cost_step2(const Planar3Params<R>& P, R* xh, R* xl, const R* u) {
+    Kin<R> k;
+    kinematics(P, xh, k);
+    R l = P.wtau * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const R inv = R(0.5) / (P.bsig * P.bsig);
+    for (int b = 0; b < P.nb; ++b) {
+      R dx = k.P[3][0] - P.bc[b][0], dy = k.P[3][1] - P.bc[b][1];
+      l += P.bamp * exp(-(dx * dx + dy * dy) * inv);
+    }
+    R qdd[3], L[9];
+    forward_dynamics(P, k, xh + 3, u, qdd, L);
+    semi_implicit2<R, 3>(xh, xl, xh + 3, xl + 3, qdd, P.dt);
+    return l;
+  }
+
   // end-effector Jacobian J (2x3) and the second-derivative structure:
   // d2 ee / dq_i dq_j = -(ee - P_max(i,j))
   template <class R>
@@ -333,15 +350,16 @@ struct SysPlanar3 {
     ee_derivs(k, ee, J);
     R gee[2] = {0, 0}, H[2][2] = {{0, 0}, {0, 0}};
     const R s2 = P.bsig * P.bsig;
-    const R inv = R(1) / (R(2) * s2);
+    const R is2 = R(1) / s2, inv = R(0.5) * is2;
     for (int b = 0; b < P.nb; ++b) {
-      R d0 = ee[0] - P.bc[b][0], d1 = ee[1] - P.bc[b][1];
-      R e = P.bamp * exp(-(d0 * d0 + d1 * d1) * inv);
-      gee[0] -= e * d0 / s2;
-      gee[1] -= e * d1 / s2;
-      H[0][0] += e * (d0 * d0 / (s2 * s2) - R(1) / s2);
-      H[1][1] += e * (d1 * d1 / (s2 * s2) - R(1) / s2);
-      H[0][1] += e * d0 * d1 / (s2 * s2);
+      const R d0 = ee[0] - P.bc[b][0], d1 = ee[1] - P.bc[b][1];
+      const R e = P.bamp * exp(-(d0 * d0 + d1 * d1) * inv);
+      const R g0 = d0 * is2, g1 = d1 * is2;     // gradient of the exponent / -1
+      gee[0] -= e * g0;
+      gee[1] -= e * g1;
+      H[0][0] += e * (g0 * g0 - is2);
+      H[1][1] += e * (g1 * g1 - is2);
+      H[0][1] += e * g0 * g1;
     }
     H[1][0] = H[0][1];
     assemble_q_block(k, ee, J, gee, H, eps, lxx, lx);

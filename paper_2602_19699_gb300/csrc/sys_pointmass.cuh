@@ -55,6 +55,17 @@ struct SysPointMass {
     step(P, x, u, xn);
     return l;
   }
+  // the same step on a state carried as (hi, lo) pairs, in place
+  template <class R>
+  TO_DEV static R cost_step2(const ParamsT<R>& P, R* xh, R* xl, const R* u) {
+    const R l = running_cost(P, xh, u);
+    const R dpx = P.dt * xh[2] + P.dt * xl[2], dpy = P.dt * xh[3] + P.dt * xl[3];
+    acc2(xh[0], xl[0], dpx);
+    acc2(xh[1], xl[1], dpy);
+    acc2(xh[2], xl[2], P.dt * u[0]);
+    acc2(xh[3], xl[3], P.dt * u[1]);
+    return l;
+  }
 
   template <class R>
   TO_DEV static R terminal_cost(const ParamsT<R>& P, const R* x) {

@@ -500,6 +500,19 @@ struct SysRigid {
     step(P, x, u, xn);
     return l;
   }
+  // the same step on a state carried as (hi, lo) pairs, in place
+  template <class R>
+  TO_DEV static R cost_step2(const ParamsT<R>& P, R* xh, R* xl, const R* u) {
+    const R l = running_cost(P, xh, u);
+    R tau[N], qdd[N], L[N * N];
+    for (int i = 0; i < N; ++i) tau[i] = i < A0 ? R(0) : u[i - A0];
+    const R h = P.dt / (R)P.n_sub;
+    for (int s = 0; s < P.n_sub; ++s) {
+      accel(P, xh, xh + N, tau, qdd, L);
+      semi_implicit2<R, N>(xh, xl, xh + N, xl + N, qdd, h);
+    }
+    return l;
+  }
   template <class R>
   TO_DEV static R terminal_cost(const ParamsT<R>& P, const R* x) {
     R l = 0;

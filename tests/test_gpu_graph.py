@@ -6,7 +6,8 @@
   the staging between replays (other initial states, other horizons) are
   picked up;
 * the launch shape changes the schedule, not the arithmetic: solves at every
-  supported shape agree;
+  supported shape agree (to the rounding of the compiler's multiply-add
+  fusion, which may differ between kernel instantiations);
 * totune measures every valid shape, returns the fastest, and later solves
   with an unset shape use it.
 """
@@ -74,9 +75,11 @@ def test_launch_shape_does_not_change_results(P):
         if ref is None:
             ref = r
             continue
+        # each shape is its own kernel instantiation: the compiler may fuse
+        # a different multiply-add pair, so equal up to that rounding
         np.testing.assert_array_equal(r["iters"], ref["iters"])
-        np.testing.assert_array_equal(r["J"], ref["J"])
-        np.testing.assert_array_equal(r["X"], ref["X"])
+        np.testing.assert_allclose(r["J"], ref["J"], rtol=1e-11, atol=0)
+        np.testing.assert_allclose(r["X"], ref["X"], rtol=0, atol=1e-11 * np.abs(ref["X"]).max())
 
 
 def test_totune_picks_the_fastest_and_caches_it(P):

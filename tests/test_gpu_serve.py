@@ -90,7 +90,8 @@ def test_admission_by_hbm_budget(P):
     h = P.tocreate_problem(prob.sys, prob.params, 50)
     opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=10)
     # a budget that holds exactly one request workspace
-    per_seat = 51 * (17 * 8 + 12) * 4 + 11 * 12 + 64
+    # knot record x, u, x_lo padded to 12 floats; gain record 10 -> 12 floats
+    per_seat = 51 * (17 * 12 + 12) * 4 + 11 * 12 + 64
     server = P.Server([h], opts, hbm_budget_bytes=per_seat + 100)
     assert server.stats()["seats"] == 1
     x = W.make_batch(prob, 2, seed=1).x0
