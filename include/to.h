@@ -214,6 +214,18 @@ int toget_trajectories(to_batch b, double* X, double* U, double* J, int* iters, 
  * warm-start cost).  Either pointer may be NULL. */
 int toget_history(to_batch b, int* alpha_idx, double* J_hist);
 
+/* Critic targets of the last solve (Sec. II: for every state of every
+ * optimised trajectory, the partial K-step cost-to-go that, with V_x from the
+ * DDP backward pass, trains the critic):
+ *     Vbar[b][k] = sum_{j=k}^{min(k+K, T_b)-1} l_j(x_j, u_j) + [k + K >= T_b] l_T(x_T)
+ * for k = 0..T_b (the terminal knot gets l_T alone), 0 for k > T_b; the
+ * state K steps ahead is X[b][min(k+K, T_b)].  Evaluated on the device in
+ * float64 from the returned trajectories (one pass over the knots, then the
+ * window sums).  Vbar: host B x (T_max+1).  V_x comes from
+ * toget_trajectories of a solve with want_vx.  Synchronises the batch's
+ * stream.  Errors: TO_ERR_ARG (K < 1, no solve), TO_ERR_CUDA. */
+int toget_critic_targets(to_batch b, int K, double* Vbar);
+
 /* Device-resident results of the last solve (no copy): J (float64, B),
  * iters and status (int32, B), in the batch's own memory. */
 int toget_device_results(to_batch b, const double** d_J, const int** d_iters, const int** d_status);

@@ -165,6 +165,14 @@ class Oracle:
         self._call("oracle_rollout", T, _d(x0), _d(U), _d(X), C.byref(J))
         return X, J.value
 
+    def critic_targets(self, X, U, K):
+        """Partial K-step cost-to-go at every knot of one trajectory (T+1 values)."""
+        X, U = _arr(X), _arr(U)
+        T = U.shape[0]
+        Vbar = np.empty(T + 1)
+        self._call("oracle_critic_targets", T, int(K), _d(X), _d(U), _d(Vbar))
+        return Vbar
+
     def backward(self, X, U, eps=1e-8):
         X, U = _arr(X), _arr(U)
         T = U.shape[0]

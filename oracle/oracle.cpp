@@ -1021,6 +1021,23 @@ int oracle_rollout(int sys, const double* p, int np, int T, const double* x0, co
   return 0;
 }
 
+// critic targets of one trajectory (Sec. II): the partial K-step cost-to-go
+// Vbar_k = sum_{j=k}^{min(k+K,T)-1} l_j(x_j, u_j) + [k + K >= T] l_T(x_T),
+// k = 0..T, summed in order from the definition
+int oracle_critic_targets(int sys, const double* p, int np, int T, int K, const double* X, const double* U,
+                          double* Vbar) {
+  Model md;
+  if (!parse(sys, p, np, md) || K < 1) return -1;
+  const int n = md.n, m = md.m;
+  for (int k = 0; k <= T; ++k) {
+    double s = 0.0;
+    for (int j = k; j < std::min(k + K, T); ++j) s += running_cost(md, X + (size_t)j * n, U + (size_t)j * m);
+    if (k + K >= T) s += terminal_cost(md, X + (size_t)T * n);
+    Vbar[k] = s;
+  }
+  return 0;
+}
+
 // one backward pass at (X, U)
 int oracle_backward(int sys, const double* p, int np, int T, const double* X, const double* U, double eps,
                     double* K, double* kff, double* Vx) {

@@ -83,6 +83,7 @@ def lib():
             L.topoll.argtypes = [vp, C.c_uint64, vp, vp, vp, vp, vp, vp]
             L.toserver_stats.argtypes = [vp, vp, vp, vp, vp]
             L.toserve_replay.argtypes = [vp, i, vp, vp, vp, vp, i, vp, vp, vp, d]
+            L.toget_critic_targets.argtypes = [vp, i, vp]
             L.totune.argtypes = [vp, i, vp, vp, C.POINTER(to_solver_opts), vp, i, vp]
             L.tograph_create.argtypes = [vp, vp, vp, i, C.POINTER(to_solver_opts), i, C.POINTER(vp)]
             L.tograph_staging.argtypes = [vp, i] + [C.POINTER(vp)] * 7
@@ -103,7 +104,7 @@ def exported_symbols():
             "tosolve_batch", "tosolve_batch_device", "toget_trajectories", "toget_history",
             "toget_device_results", "tolast_launch_count", "toget_phase_cycles", "tosolve_batch_noalloc",
             "toserver_create", "toserver_destroy", "tosubmit", "topoll", "toserver_stats", "toserve_replay",
-            "totune", "tograph_create", "tograph_staging", "tograph_launch", "tograph_sync", "tograph_launch_count",
+            "toget_critic_targets", "totune", "tograph_create", "tograph_staging", "tograph_launch", "tograph_sync", "tograph_launch_count",
             "tograph_destroy", "tolast_error"]
 
 
@@ -396,6 +397,13 @@ def toget_trajectories(batch: Batch, X=True, U=True, Vx=False, K=False) -> dict:
     }
     _check(lib().toget_trajectories(batch.handle, _ptr(out["X"]), _ptr(out["U"]), _ptr(out["J"]),
                                     _ptr(out["iters"]), _ptr(out["status"]), _ptr(out["Vx"]), _ptr(out["K"])))
+    return out
+
+
+def toget_critic_targets(batch: Batch, K: int) -> np.ndarray:
+    """Partial K-step cost-to-go of every knot of the last solve, B x (T_max+1)."""
+    out = np.empty((batch.B, batch.problem.T_max + 1))
+    _check(lib().toget_critic_targets(batch.handle, int(K), _ptr(out)))
     return out
 
 

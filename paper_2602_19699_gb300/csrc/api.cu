@@ -143,6 +143,27 @@ __global__ void gather_kernel(int B, int T_max, int n, int m, int RS, int GS, in
   }
 }
 
+// Vbar_k = sum_{j=k}^{min(k+K,T)-1} l_j + [k + K >= T] l_T over the per-knot
+// costs l (B x (T_max+1)); 0 past T.  One thread per knot, summed in order.
+__global__ void window_kernel(int B, int T_max, int K, const int* __restrict__ T, const double* __restrict__ l,
+                              double* __restrict__ Vbar) {
+  const long long total = (long long)B * (T_max + 1);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / (T_max + 1)), k = (int)(t % (T_max + 1));
+    const int Tb = T[b];
+    if (k > Tb) {
+      Vbar[t] = 0.0;
+      continue;
+    }
+    const double* lb = l + (long long)b * (T_max + 1);
+    const int end = min(k + K, Tb);
+    double s = 0.0;
+    for (int j = k; j < end; ++j) s += lb[j];
+    if (k + K >= Tb) s += lb[Tb];
+    Vbar[t] = s;
+  }
+}
+
 }  // namespace to
 
 // ===========================================================================
@@ -592,6 +613,40 @@ int toget_trajectories(to_batch b, double* X, double* U, double* J, int* iters, 
   if (iters) TO_CK(cudaMemcpyAsync(iters, b->iters, B * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   if (status) TO_CK(cudaMemcpyAsync(status, b->status, B * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   TO_CK(cudaStreamSynchronize(b->stream));
+  return TO_OK;
+}
+
+int toget_critic_targets(to_batch b, int K, double* Vbar) {
+  if (!b || !Vbar || K < 1) return fail(TO_ERR_ARG, "toget_critic_targets: null batch / output or K < 1");
+  to_problem p = b->p;
+  const int B = b->B;
+  TO_CK(cudaStreamSynchronize(b->stream));
+  if (B == 0) return TO_OK;
+  if (!b->last_T) return fail(TO_ERR_ARG, "toget_critic_targets: the batch holds no solve");
+  const size_t cnt = (size_t)B * (p->T_max + 1);
+  double* d = nullptr;
+  TO_CK(cudaMalloc(&d, 2 * cnt * sizeof(double)));
+  KnotCostArgs ka{};
+  ka.B = B;
+  ka.T_max = p->T_max;
+  ka.NS = std::min(b->G, kLsWidth) + 1;
+  ka.rbytes = b->prec == TO_FP64 ? 8 : 4;
+  ka.RS = p->ops->rs[ka.rbytes == 8 ? 0 : 1];
+  ka.toff = b->toff;
+  ka.T = b->last_T;
+  ka.slot = b->slot;
+  ka.traj = b->traj;
+  ka.params64 = p->d_params[0];
+  ka.out = d;
+  cudaError_t e = p->ops->knot_costs(ka, b->stream);
+  if (e == cudaSuccess) {
+    window_kernel<<<1024, 256, 0, b->stream>>>(B, p->T_max, K, b->last_T, d, d + cnt);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Vbar, d + cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("toget_critic_targets: ") + cudaGetErrorString(e));
   return TO_OK;
 }
 

@@ -2,12 +2,24 @@
 // units.  Each system TU instantiates the solver for FP64 and mixed arithmetic
 // and the group sizes it supports, and registers a SysOps table.
 #pragma once
+#include <algorithm>
 #include <string>
 #include <vector>
 
 #include "ilqr.cuh"
 
 namespace to {
+
+// inputs of the per-knot cost pass over a batch's returned trajectories
+struct KnotCostArgs {
+  int B, T_max, NS, RS, rbytes;
+  const long long* toff;
+  const int* T;
+  const int* slot;
+  const void* traj;
+  const void* params64;     // the system's parameter struct in float64
+  double* out;              // B x (T_max + 1): l_k(x_k, u_k) for k < T, l_T(x_T) at k = T, 0 beyond
+};
 
 struct SysOps {
   int sys, n, m;
@@ -21,6 +33,8 @@ struct SysOps {
                std::string& err);
   cudaError_t (*launch)(int prec, int G, int gpb, int grid, cudaStream_t s, const SolveArgs& a);
   cudaError_t (*occupancy)(int prec, int G, int gpb, size_t* smem, int* blocks_per_sm);
+  // per-knot costs of the final trajectories in float64 (critic targets)
+  cudaError_t (*knot_costs)(const KnotCostArgs& a, cudaStream_t s);
 };
 
 const SysOps* sys_ops(int sys);
@@ -83,6 +97,59 @@ struct Dispatch<Sys, G0, Gs...> {
     return Dispatch<Sys, Gs...>::occupancy(prec, G, gpb, smem, bps);
   }
 };
+
+// One thread per knot: the state is rebuilt in float64 from the record
+// (float32 records add the low parts stored after u) and the system's own
+// cost functions evaluate l_k or l_T in float64.
+template <class Sys>
+__global__ void knot_cost_kernel(KnotCostArgs a) {
+  typedef typename Sys::template ParamsT<double> PD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  {
+    const int words = (int)(sizeof(PD) / sizeof(int));
+    for (int i = threadIdx.x; i < words; i += blockDim.x)
+      reinterpret_cast<int*>(smem_raw)[i] = reinterpret_cast<const int*>(a.params64)[i];
+  }
+  __syncthreads();
+  const PD& P = *reinterpret_cast<const PD*>(smem_raw);
+  constexpr int n = Sys::n, m = Sys::m;
+  const long long total = (long long)a.B * (a.T_max + 1);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / (a.T_max + 1)), k = (int)(t % (a.T_max + 1));
+    const int Tb = a.T[b];
+    if (k > Tb) {
+      a.out[t] = 0.0;
+      continue;
+    }
+    const long long r = ((a.toff[b] + k) * a.NS + a.slot[b]) * a.RS;
+    double x[n], u[m];
+    for (int i = 0; i < n; ++i)
+      x[i] = a.rbytes == 8 ? reinterpret_cast<const double*>(a.traj)[r + i]
+                           : (double)reinterpret_cast<const float*>(a.traj)[r + i] +
+                                 (double)reinterpret_cast<const float*>(a.traj)[r + n + m + i];
+    if (k < Tb) {
+      for (int i = 0; i < m; ++i)
+        u[i] = a.rbytes == 8 ? reinterpret_cast<const double*>(a.traj)[r + n + i]
+                             : (double)reinterpret_cast<const float*>(a.traj)[r + n + i];
+      a.out[t] = Sys::template running_cost<double>(P, x, u);
+    } else {
+      a.out[t] = Sys::template terminal_cost<double>(P, x);
+    }
+  }
+}
+
+template <class Sys>
+inline cudaError_t knot_costs_one(const KnotCostArgs& a, cudaStream_t s) {
+  const size_t smem = (sizeof(typename Sys::template ParamsT<double>) + 15) / 16 * 16;
+  auto k = knot_cost_kernel<Sys>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)a.B * (a.T_max + 1);
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+  k<<<grid, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 template <class Sys>
 inline void fill_layout(SysOps& o) {

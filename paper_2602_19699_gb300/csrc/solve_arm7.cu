@@ -43,6 +43,7 @@ static SysOps make_ops() {
   o.parse = parse_arm7;
   o.launch = A7Dispatch::launch;
   o.occupancy = A7Dispatch::occupancy;
+  o.knot_costs = knot_costs_one<SysArm7>;
   return o;
 }
 

@@ -56,6 +56,7 @@ static SysOps make_ops() {
   o.parse = parse_planar3;
   o.launch = P3Dispatch::launch;
   o.occupancy = P3Dispatch::occupancy;
+  o.knot_costs = knot_costs_one<SysPlanar3>;
   return o;
 }
 

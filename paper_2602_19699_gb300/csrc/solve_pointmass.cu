@@ -35,6 +35,7 @@ static SysOps make_ops() {
   o.parse = parse_pointmass;
   o.launch = PMDispatch::launch;
   o.occupancy = PMDispatch::occupancy;
+  o.knot_costs = knot_costs_one<SysPointMass>;
   return o;
 }
 

@@ -43,6 +43,7 @@ static SysOps make_ops() {
   o.parse = parse_quad;
   o.launch = QDispatch::launch;
   o.occupancy = QDispatch::occupancy;
+  o.knot_costs = knot_costs_one<SysQuad>;
   return o;
 }
 
