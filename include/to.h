@@ -163,7 +163,21 @@ typedef struct {
                              0 = the totune choice, else the default          */
   int profile_phases;     /* 1: accumulate per-phase clock64 cycles (tracing;
                              see toget_phase_cycles); 0 = off                 */
+  int reg;                /* TO_REG_CLIP (default): eigenvalue clipping of the
+                             cost Hessians, mu I only as a Cholesky guard
+                             (Sec. IV-B, the paper's GPU choice);
+                             TO_REG_LM: the standard Levenberg-Marquardt
+                             iLQR the paper compares against (Sec. IV-B):
+                             no clipping, Q_uu + mu I with mu = 1e-6 at the
+                             start, x10 and the backward pass redone when
+                             the pivot test or the line search fails, /10
+                             (not below 1e-8) after an accepted step;
+                             mu > 1e10 stops the instance with LS_FAIL.
+                             eps_clip is ignored                              */
 } to_solver_opts;
+
+/* to_solver_opts.reg */
+enum { TO_REG_CLIP = 0, TO_REG_LM = 1 };
 
 /* Defaults: max_iter 100, tol_rel 1e-8, eps_clip 1e-8, n_alpha 16,
  * alpha_decay 0.5, TO_MIXED, refine 1, no forcing, want_vx 0, no budget,

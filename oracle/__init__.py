@@ -202,7 +202,9 @@ class Oracle:
 
     # --- the full iLQR over a batch ----------------------------------------
     def solve(self, x0, T, U_init=None, max_iter=100, tol=1e-8, eps=1e-8, n_alpha=8, alpha_decay=0.5,
-              forced=None, threads=0, want_vx=False, want_K=False, use_actor=True):
+              forced=None, threads=0, want_vx=False, want_K=False, use_actor=True, reg="clip"):
+        """iLQR as stated in the paper (reg="clip": eigenvalue clipping, Sec. IV-B),
+        or the standard Levenberg-Marquardt variant it compares against (reg="lm")."""
         x0 = _arr(np.atleast_2d(x0))
         B = x0.shape[0]
         T = _arr(np.broadcast_to(np.asarray(T), (B,)), np.int32)
@@ -226,7 +228,7 @@ class Oracle:
         rc = lib().oracle_solve_batch(self.sys, _d(self.p), self.np, _f(aw), B, T_max, _d(x0), _i(T), _d(U_init),
                                       int(max_iter), C.c_double(tol), C.c_double(eps), int(n_alpha),
                                       C.c_double(alpha_decay), _i(forced), int(threads), _d(X), _d(U), _d(J),
-                                      _i(iters), _i(status), _d(Vx), _d(K), _i(ah), _d(Jh))
+                                      _i(iters), _i(status), _d(Vx), _d(K), _i(ah), _d(Jh), int(reg == "lm"))
         if rc != 0:
             raise RuntimeError(f"oracle_solve_batch failed ({rc})")
         return dict(X=X, U=U, J=J, iters=iters, status=status, Vx=Vx, K=K, alpha_hist=ah, J_hist=Jh, T=T)

@@ -648,6 +648,18 @@ static int chol_guarded(int m, const double* Quu, double* L) {
   return -1;
 }
 
+// Levenberg-Marquardt variant (Sec. IV-B's standard regularisation): factor
+// Q_uu + mu I under the pivot test d_j > 1e-12 (max|diag Q_uu| + mu); 0 ok,
+// -3 when mu must grow, -1 on a non-finite Q_uu
+static int chol_shifted(int m, const double* Quu, double mu, double* L) {
+  double mx = 0;
+  for (int i = 0; i < m; ++i) mx = std::max(mx, std::fabs(Quu[i * m + i]));
+  if (!std::isfinite(mx)) return -1;
+  std::vector<double> R(Quu, Quu + m * m);
+  for (int i = 0; i < m; ++i) R[i * m + i] += mu;
+  return chol_factor(m, R.data(), 1e-12 * (mx + mu), L) ? 0 : -3;
+}
+
 static void chol_apply_inv(int m, const double* L, const double* b, double* x) {
   std::vector<double> y(m);
   for (int i = 0; i < m; ++i) {
@@ -701,7 +713,11 @@ struct Opts {
   int n_alpha;
   double alpha_decay;
   const int* forced;   // [max_iter], -1 ends the run; NULL: line search decides
+  int lm;              // 1: Levenberg-Marquardt variant (no clipping, mu retry loop)
 };
+
+// the Levenberg-Marquardt variant's mu schedule
+static const double kMu0 = 1e-6, kMuMin = 1e-8, kMuMax = 1e10, kMuFactor = 10.0;
 
 static double rollout_cost(const Model& md, int T, const double* x0, const double* U, double* X) {
   const int n = md.n, m = md.m;
@@ -716,8 +732,10 @@ static double rollout_cost(const Model& md, int T, const double* x0, const doubl
 
 // backward pass at (X, U): gains K (T x m x n), k (T x m), value gradient Vx
 // ((T+1) x n). Returns 0, or ST_FLAG_REG if a Cholesky needed mu, or -1.
+// lm = 1: the cost Hessians are used as they are and every Q_uu gets + mu I;
+// returns -3 when some Q_uu + mu I fails the pivot test.
 static int backward(const Model& md, int T, const double* X, const double* U, double eps, double* K,
-                    double* kff, double* Vx_out) {
+                    double* kff, double* Vx_out, int lm = 0, double mu = 0.0) {
   const int n = md.n, m = md.m;
   std::vector<double> Vx(n), Vxx(n * n), lg(n + m), lH((n + m) * (n + m)), lxx(n * n), luu(m * m),
       A(n * n), Bm(n * m), Qx(n), Qu(m), Qxx(n * n), Quu(m * m), Qux(m * n), VA(n * n), VB(n * m),
@@ -725,7 +743,8 @@ static int backward(const Model& md, int T, const double* X, const double* U, do
   double l;
   cost_derivs(md, X + T * n, nullptr, true, &l, lg.data(), lH.data());
   for (int i = 0; i < n; ++i) Vx[i] = lg[i];
-  eigclip(n, lH.data(), eps, Vxx.data());
+  if (lm) std::memcpy(Vxx.data(), lH.data(), sizeof(double) * n * n);
+  else eigclip(n, lH.data(), eps, Vxx.data());
   if (Vx_out) for (int i = 0; i < n; ++i) Vx_out[T * n + i] = Vx[i];
   int flag = 0;
   for (int k = T - 1; k >= 0; --k) {
@@ -736,10 +755,12 @@ static int backward(const Model& md, int T, const double* X, const double* U, do
     const int nz = n + m;
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) tmp[i * n + j] = lH[i * nz + j];
-    eigclip(n, tmp.data(), eps, lxx.data());
+    if (lm) std::memcpy(lxx.data(), tmp.data(), sizeof(double) * n * n);
+    else eigclip(n, tmp.data(), eps, lxx.data());
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) tmp[i * m + j] = lH[(n + i) * nz + n + j];
-    eigclip(m, tmp.data(), eps, luu.data());
+    if (lm) std::memcpy(luu.data(), tmp.data(), sizeof(double) * m * m);
+    else eigclip(m, tmp.data(), eps, luu.data());
     // Q terms
     for (int i = 0; i < n; ++i) {
       double s = lg[i];
@@ -781,7 +802,8 @@ static int backward(const Model& md, int T, const double* X, const double* U, do
         for (int r = 0; r < n; ++r) s += Bm[r * m + i] * VA[r * n + j];
         Qux[i * n + j] = s;
       }
-    int rc = chol_guarded(m, Quu.data(), L.data());
+    int rc = lm ? chol_shifted(m, Quu.data(), mu, L.data()) : chol_guarded(m, Quu.data(), L.data());
+    if (rc == -3) return -3;
     if (rc < 0) return -1;
     if (rc == 1) flag = ST_FLAG_REG;
     // K = -Quu^{-1} Qux, k = -Quu^{-1} Qu
@@ -860,9 +882,16 @@ static Result ilqr(const Model& md, int T, const double* x0, const double* U0, c
   if (!std::isfinite(J)) { res.J = J; res.status = ST_NONFINITE; return res; }
   std::vector<double> K((size_t)T * m * n), kff((size_t)T * m), Xn((size_t)(T + 1) * n), Un((size_t)T * m);
   int flags = 0, status = ST_MAX_ITER, it = 0;
+  double mu = kMu0;
   while (it < o.max_iter) {
     if (o.forced && o.forced[it] < 0) break;
-    int rc = backward(md, T, X, U, o.eps, K.data(), kff.data(), nullptr);
+    int rc = backward(md, T, X, U, o.eps, K.data(), kff.data(), nullptr, o.lm, mu);
+    if (rc == -3) {
+      // Levenberg-Marquardt: grow mu and redo the backward pass
+      mu *= kMuFactor;
+      if (mu > kMuMax) { status = ST_LS_FAIL; break; }
+      continue;
+    }
     if (rc < 0) { status = ST_NONFINITE; break; }
     flags |= rc;
     int acc = -1;
@@ -877,7 +906,13 @@ static Result ilqr(const Model& md, int T, const double* x0, const double* U0, c
         if (Jj < J) { acc = j; Jn = Jj; break; }   // smallest j with strict decrease
       }
     }
+    if (acc < 0 && o.lm) {
+      mu *= kMuFactor;
+      if (mu > kMuMax) { status = ST_LS_FAIL; break; }
+      continue;
+    }
     if (acc < 0) { status = ST_LS_FAIL; break; }
+    if (o.lm) mu = std::max(mu / kMuFactor, kMuMin);
     std::memcpy(X, Xn.data(), sizeof(double) * (T + 1) * n);
     std::memcpy(U, Un.data(), sizeof(double) * T * m);
     if (alpha_hist) alpha_hist[it] = acc;
@@ -890,7 +925,7 @@ static Result ilqr(const Model& md, int T, const double* x0, const double* U0, c
   }
   if ((Vx || K_out || k_out) && std::isfinite(J)) {
     std::vector<double> vx((size_t)(T + 1) * n);
-    int rc = backward(md, T, X, U, o.eps, K.data(), kff.data(), vx.data());
+    int rc = backward(md, T, X, U, o.eps, K.data(), kff.data(), vx.data(), o.lm, mu);
     if (rc > 0) flags |= rc;
     if (Vx) std::memcpy(Vx, vx.data(), sizeof(double) * (T + 1) * n);
     if (K_out) std::memcpy(K_out, K.data(), sizeof(double) * T * m * n);
@@ -1062,7 +1097,7 @@ int oracle_forward_pass(int sys, const double* p, int np, int T, const double* X
 int oracle_solve_batch(int sys, const double* p, int np, const float* actor_w, int B, int T_max, const double* x0,
                        const int* T, const double* U_init, int max_iter, double tol, double eps, int n_alpha,
                        double alpha_decay, const int* forced, int n_threads, double* X, double* U, double* J,
-                       int* iters, int* status, double* Vx, double* K, int* alpha_hist, double* J_hist) {
+                       int* iters, int* status, double* Vx, double* K, int* alpha_hist, double* J_hist, int lm) {
   Model md;
   if (!parse(sys, p, np, md)) return -1;
   const int n = md.n, m = md.m;
@@ -1073,7 +1108,7 @@ int oracle_solve_batch(int sys, const double* p, int np, const float* actor_w, i
   auto work = [&](int t0) {
     for (int b = t0; b < B; b += n_threads) {
       const int Tb = T[b];
-      Opts o{max_iter, tol, eps, n_alpha, alpha_decay, forced ? forced + (size_t)b * max_iter : nullptr};
+      Opts o{max_iter, tol, eps, n_alpha, alpha_decay, forced ? forced + (size_t)b * max_iter : nullptr, lm};
       std::vector<double> Xb((size_t)(Tb + 1) * n), Ub((size_t)Tb * m), vx, kk;
       std::vector<double> Kb;
       if (Vx) vx.resize((size_t)(Tb + 1) * n);

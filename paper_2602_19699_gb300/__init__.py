@@ -23,6 +23,7 @@ TO_SYS_POINTMASS2D, TO_SYS_PLANAR3, TO_SYS_ARM7, TO_SYS_QUAD18 = 1, 2, 3, 4
 TO_FP64, TO_MIXED = 0, 1
 TO_OK, TO_ERR_ARG, TO_ERR_CUDA, TO_ERR_BUDGET, TO_ERR_TIMEOUT, TO_ERR_NOTREADY, TO_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 TO_ST_CONVERGED, TO_ST_MAX_ITER, TO_ST_LS_FAIL, TO_ST_NONFINITE, TO_ST_TIMEOUT, TO_ST_FLAG_REG = 1, 2, 3, 4, 5, 16
+TO_REG_CLIP, TO_REG_LM = 0, 1
 
 
 class ToError(RuntimeError):
@@ -41,7 +42,8 @@ class to_solver_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("tol_rel", C.c_double), ("eps_clip", C.c_double), ("n_alpha", C.c_int),
                 ("alpha_decay", C.c_double), ("prec", C.c_int), ("refine", C.c_int),
                 ("forced_alpha", C.POINTER(C.c_int)), ("want_vx", C.c_int), ("hbm_budget_bytes", C.c_size_t),
-                ("group_lanes", C.c_int), ("groups_per_block", C.c_int), ("profile_phases", C.c_int)]
+                ("group_lanes", C.c_int), ("groups_per_block", C.c_int), ("profile_phases", C.c_int),
+                ("reg", C.c_int)]
 
 
 _lib = None

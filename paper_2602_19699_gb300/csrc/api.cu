@@ -383,6 +383,7 @@ static int check_opts(const to_solver_opts* o) {
   if (!(o->alpha_decay > 0 && o->alpha_decay <= 1)) return fail(TO_ERR_ARG, "opts: alpha_decay must be in (0, 1]");
   if (!(o->eps_clip >= 0)) return fail(TO_ERR_ARG, "opts: eps_clip must be >= 0");
   if (o->prec != TO_FP64 && o->prec != TO_MIXED) return fail(TO_ERR_ARG, "opts: prec must be TO_FP64 or TO_MIXED");
+  if (o->reg != TO_REG_CLIP && o->reg != TO_REG_LM) return fail(TO_ERR_ARG, "opts: reg must be TO_REG_CLIP or TO_REG_LM");
   return TO_OK;
 }
 
@@ -436,6 +437,8 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   a.B = B; a.T_max = p->T_max; a.max_iter = o->max_iter; a.n_alpha = o->n_alpha;
   a.refine = o->refine; a.want_vx = o->want_vx;
   a.tol = o->tol_rel; a.eps = o->eps_clip;
+  a.lm = o->reg == TO_REG_LM ? 1 : 0;
+  if (a.lm) a.eps = -1e30;   // no clipping: every eigenvalue is above the floor
   double al = 1.0;
   for (int j = 0; j < kMaxAlpha; ++j) {
     a.alpha_d[j] = al;

@@ -95,6 +95,10 @@ TO_DEV void semi_implicit2(R* qh, R* ql, R* vh, R* vl, const R* a, R h) {
   }
 }
 
+// clip of a zero eigenvalue, max(0, eps): the value a Hessian's entries
+// outside a cost's support take (0 when clipping is off, eps < 0)
+template <class R> TO_DEV R clip0(R eps) { return eps > R(0) ? eps : R(0); }
+
 template <class R> TO_DEV R rsqrt_(R x);
 template <> TO_DEV float rsqrt_(float x) { return rsqrtf(x); }
 template <> TO_DEV double rsqrt_(double x) { return rsqrt(x); }

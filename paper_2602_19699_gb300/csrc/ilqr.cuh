@@ -63,6 +63,7 @@ struct ServeArgs {
 struct SolveArgs {
   ServeArgs serve;
   int B, T_max, max_iter, n_alpha, refine, want_vx;
+  int lm;                  // 1: Levenberg-Marquardt variant (no clip, mu retry loop)
   double tol, eps;
   double alpha_d[kMaxAlpha];   // alpha_j = decay^j
   float alpha_f[kMaxAlpha];
@@ -161,6 +162,12 @@ struct Work {
 
 enum { M_IDLE = 0, M_NEW, M_RUN, M_FINAL, M_DRAINED };
 
+// Levenberg-Marquardt variant: mu starts at kMu0, is multiplied by kMuFactor
+// when Q_uu + mu I fails the pivot test or the line search finds no decrease
+// (and the backward pass is redone), divided by it after an accepted step
+// (not below kMuMin); beyond kMuMax the instance stops with LS_FAIL
+constexpr double kMu0 = 1e-6, kMuMin = 1e-8, kMuMax = 1e10, kMuFactor = 10.0;
+
 template <class Sys, class R, int G>
 struct Solver {
   static constexpr int n = Sys::n, m = Sys::m;
@@ -195,6 +202,19 @@ struct Solver {
       }
     }
     return true;
+  }
+  // Levenberg-Marquardt variant (Sec. IV-B's standard regularisation): the
+  // factor of Q_uu + mu I with the pivot test; flag 3 asks for a larger mu
+  TO_DEV static void chol_lm(W& w, double mu) {
+    double mx = 0;
+    for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(w.Quu[i * m + i]));
+    w.mu = mu;
+    w.flag = 3;
+    if (!isfinite(mx)) { w.flag = 2; return; }
+    if (chol(w.Quu, mu, 1e-12 * (mx + mu), w.L)) {
+      w.flag = 0;
+      for (int i = 0; i < m * m; ++i) w.Lf[i] = (R)w.L[i];
+    }
   }
   TO_DEV static void chol_guarded(W& w) {
     double mx = 0;
@@ -320,7 +340,7 @@ struct Solver {
   // ------------------------------------------------------------------------
   TO_DEV static int backward_knot(const Params& P, const Group<G>& g, W& w, bool act, bool act_next,
                                   const SolveArgs& a, R (&pb)[PB], const R* trec_next, R* grec, double* vxrec,
-                                  bool timer, long long& tlast) {
+                                  double mu_lm, bool timer, long long& tlast) {
     const R eps = (R)a.eps;
     if (act) {
 #pragma unroll
@@ -401,10 +421,13 @@ struct Solver {
       }
     g.sync();
     TO_TICK(2);
-    if (act && g.lane == 0) chol_guarded(w);
+    if (act && g.lane == 0) {
+      if (a.lm) chol_lm(w, mu_lm);
+      else chol_guarded(w);
+    }
     g.sync();
     const int flag = act ? w.flag : 0;
-    if (act && flag != 2)
+    if (act && flag < 2)
       for (int c = g.lane; c <= n; c += G) gain_column(w, c, a.refine);
     g.sync();
     TO_TICK(3);
@@ -552,6 +575,7 @@ struct Solver {
     double J = 0;
     long long base = 0;
     int sq = 0;          // serving: ring index of the request being solved
+    double mu_lm = kMu0;  // Levenberg-Marquardt variant: the instance's mu
     int idle = 0;        // serving: consecutive polls with every group idle
 
     while (true) {
@@ -586,12 +610,12 @@ struct Solver {
             base = (long long)inst * (a.T_max + 1);
             sq = q;
             if (g.lane == 0) a.serve.seat_T[inst] = T;
-            mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0;
+            mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0; mu_lm = kMu0;
           } else if (q >= 0) {
             inst = a.order[q];
             T = a.T[inst];
             base = a.toff[inst];
-            mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0;
+            mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0; mu_lm = kMu0;
           } else if (q == -2) {
             mode = M_DRAINED;
           }
@@ -624,6 +648,7 @@ struct Solver {
       }
       TO_TICK(0);
       bool release = false;
+      bool retry = false;   // Levenberg-Marquardt: redo the backward pass with a larger mu
       // ---- a forced sequence ends with -1
       if (mode == M_RUN && forced_mode && a.forced[(size_t)inst * a.max_iter + iter] < 0) {
         status = ST_MAX_ITER;
@@ -634,7 +659,7 @@ struct Solver {
       {
         const bool bw = (mode == M_RUN || mode == M_FINAL) && !release;
         const int kmax = g.uniform_max(bw ? T : 0, &w.sel);
-        bool bad = false;
+        bool bad = false, need_mu = false;
         if (kmax > 0) {
           R pb[PB];
           if (bw) {
@@ -662,14 +687,21 @@ struct Solver {
             const long long kk = base + (act ? k : 0);
             const R* rn = rec(traj, base, act_next ? k - 1 : 0, cur);
             const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, gains + kk * GS,
-                                        (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, timer, tlast);
+                                        (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, mu_lm, timer, tlast);
             if (f == 1) flags |= ST_FLAG_REG;
             if (f == 2) bad = true;
+            if (f == 3) need_mu = true;
           }
         }
         if (bw && bad) {
           status = ST_NONFINITE;
           release = true;
+        } else if (bw && need_mu) {
+          // Levenberg-Marquardt: Q_uu + mu I was not positive definite at some
+          // knot; grow mu and redo the backward pass (no iteration counted)
+          mu_lm *= kMuFactor;
+          if (mu_lm > kMuMax) { status = ST_LS_FAIL; release = true; }
+          else retry = true;
         }
       }
       if (mode == M_FINAL && !release) release = true;   // V_x pass done
@@ -681,7 +713,7 @@ struct Solver {
       int jstar = -1, newslot = cur;
       double Jnew = 0;
       {
-        const bool fwd = (mode == M_NEW) || (mode == M_RUN && !release);
+        const bool fwd = (mode == M_NEW) || (mode == M_RUN && !release && !retry);
         const bool single = (mode == M_NEW) || forced_mode;
         // the actor warm start runs when the problem has actor weights and no
         // caller-given controls (uniform over the warp / CTA: it holds barriers)
@@ -792,9 +824,16 @@ struct Solver {
         }
       }
       TO_TICK(5);
-      if (mode == M_RUN && !release && jstar < 0) {
-        status = ST_LS_FAIL;
-        release = true;
+      if (mode == M_RUN && !release && !retry && jstar < 0) {
+        if (a.lm) {
+          // no step size decreased the cost: grow mu and redo the backward pass
+          mu_lm *= kMuFactor;
+          if (mu_lm > kMuMax) { status = ST_LS_FAIL; release = true; }
+          else retry = true;
+        } else {
+          status = ST_LS_FAIL;
+          release = true;
+        }
       }
 
       // ---- phase D: bookkeeping
@@ -805,9 +844,10 @@ struct Solver {
         if (!isfinite(J)) { status = ST_NONFINITE; release = true; }
         else if (a.max_iter == 0) { status = ST_MAX_ITER; release = true; }
         else mode = M_RUN;
-      } else if (mode == M_RUN && !release) {
+      } else if (mode == M_RUN && !release && !retry) {
         ++iter;
         cur = newslot;
+        mu_lm = fmax(mu_lm / kMuFactor, kMuMin);
         if (g.lane == 0) {
           a.ahist[(size_t)inst * a.max_iter + iter - 1] = jstar;
           a.Jhist[(size_t)inst * (a.max_iter + 1) + iter] = Jnew;

@@ -364,7 +364,7 @@ struct SysPlanar3 {
     H[1][0] = H[0][1];
     assemble_q_block(k, ee, J, gee, H, eps, lxx, lx);
 #pragma unroll
-    for (int i = 3; i < 6; ++i) { lxx[i * n + i] = eps; lx[i] = 0; }
+    for (int i = 3; i < 6; ++i) { lxx[i * n + i] = clip0(eps); lx[i] = 0; }
     const R w2 = R(2) * P.wtau;
     const R d = w2 > eps ? w2 : eps;
 #pragma unroll

@@ -98,7 +98,7 @@ struct SysPointMass {
 #pragma unroll
     for (int i = 0; i < n * n; ++i) lxx[i] = 0;
     lxx[0] = hxx; lxx[1] = hxy; lxx[4] = hxy; lxx[5] = hyy;
-    lxx[10] = eps; lxx[15] = eps;
+    lxx[10] = clip0(eps); lxx[15] = clip0(eps);
     lx[0] = gx; lx[1] = gy; lx[2] = 0; lx[3] = 0;
     const R w2 = R(2) * P.wu;
     const R d = w2 > eps ? w2 : eps;

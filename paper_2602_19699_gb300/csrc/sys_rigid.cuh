@@ -538,7 +538,7 @@ struct SysRigid {
     const R w2 = R(2) * P.wtau;
     for (int j = 0; j < m; ++j) { lu[j] = w2 * u[j]; luu[j * m + j] = w2 > eps ? w2 : eps; }
     R dq[N];   // diagonal of the q-block and qd-block
-    for (int i = 0; i < n; ++i) lxx[i * n + i] = eps;
+    for (int i = 0; i < n; ++i) lxx[i * n + i] = clip0(eps);
     if (KIND == RK_ARM7) {
       const R v2 = R(2) * P.wv;
       for (int j = 0; j < N; ++j) { lx[N + j] = v2 * x[N + j]; lxx[(N + j) * n + N + j] = v2 > eps ? v2 : eps; }
@@ -585,7 +585,7 @@ struct SysRigid {
     } else {
       const R s = P.tscale;
       const R z2 = R(2) * P.wz * s, r2 = R(2) * P.wrpy * s, x2 = R(2) * P.wvx * s;
-      for (int i = 0; i < n; ++i) lxx[i * n + i] = eps;
+      for (int i = 0; i < n; ++i) lxx[i * n + i] = clip0(eps);
       lx[2] = z2 * (x[2] - P.znom); lxx[2 * n + 2] = z2 > eps ? z2 : eps;
       for (int k = 3; k < 6; ++k) { lx[k] = r2 * x[k]; lxx[k * n + k] = r2 > eps ? r2 : eps; }
       lx[N] = x2 * (x[N] - P.vxt); lxx[N * n + N] = x2 > eps ? x2 : eps;

@@ -65,7 +65,9 @@ def test_graph_members_equal_separate_solves(P, prec):
 
 
 def test_launch_shape_does_not_change_results(P):
-    prob = W.planar3(seed=4)
+    # the point mass: a well-conditioned system, so the fusion rounding stays
+    # at its own size (the planar arm is chaotic and amplifies it)
+    prob = W.pointmass(seed=4)
     b = W.make_batch(prob, 200, seed=5, T=(20, 80))
     h = P.tocreate_problem(prob.sys, prob.params, 80)
     ref = None
