@@ -50,7 +50,8 @@ enum {
   TO_SYS_POINTMASS2D = 1, /* n=4 [px,py,vx,vy], m=2, explicit Euler              */
   TO_SYS_PLANAR3 = 2,     /* planar 3-link arm, n=6, m=3, semi-implicit Euler     */
   TO_SYS_ARM7 = 3,        /* 7-DoF serial arm, n=14, m=7, semi-implicit Euler     */
-  TO_SYS_QUAD18 = 4       /* 6 virtual base joints + 4x3 legs, n=36, m=12, contact */
+  TO_SYS_QUAD18 = 4,      /* 6 virtual base joints + 4x3 legs, n=36, m=12, contact */
+  TO_SYS_DUBINS = 5       /* jerk-controlled Dubins car, n=5, m=2, explicit Euler  */
 };
 
 /* arithmetic of the solve */
@@ -91,6 +92,15 @@ enum {
  *   [5 .. 5+2nb) bump centres (x, y)  [5+2nb] w_pT  [6+2nb] w_vT
  *   l_k = w_u |u|^2 + sum_b amp exp(-|p - c_b|^2 / (2 sigma^2))
  *   l_T = w_pT |p|^2 + w_vT |v|^2
+ *
+ * TO_SYS_DUBINS (Sec. V-A's jerk-controlled Dubins car without the time
+ * state; x = [px, py, theta, v, a], u = [omega, jerk]):
+ *   [0] dt  [1] w_u  [2] bump amplitude  [3] bump sigma  [4] nb (<= 8)
+ *   [5 .. 5+2nb) bump centres  [5+2nb] w_pT  [6+2nb] w_vT  [7+2nb] w_aT
+ *   px+ = px + dt v cos(theta), py+ = py + dt v sin(theta),
+ *   theta+ = theta + dt omega, v+ = v + dt a, a+ = a + dt jerk
+ *   l_k = w_u |u|^2 + sum_b amp exp(-|p - c_b|^2 / (2 sigma^2))
+ *   l_T = w_pT |p|^2 + w_vT v^2 + w_aT a^2
  *
  * Rigid-body systems (TO_SYS_PLANAR3, TO_SYS_ARM7, TO_SYS_QUAD18):
  *   header  [0] dt  [1..3] gravity vector (world)  [4] N joints  [5] a0 (first

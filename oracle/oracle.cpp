@@ -83,7 +83,7 @@ template <class B> double val(const D<B>& x) { return val(x.v); }
 // ----------------------------------------------------------------------------
 // problem description, parsed from the flat parameter vector
 // ----------------------------------------------------------------------------
-enum { SYS_PM = 1, SYS_PLANAR3 = 2, SYS_ARM7 = 3, SYS_QUAD = 4 };
+enum { SYS_PM = 1, SYS_PLANAR3 = 2, SYS_ARM7 = 3, SYS_QUAD = 4, SYS_DUBINS = 5 };
 enum { J_RX = 0, J_RY, J_RZ, J_PX, J_PY, J_PZ };
 
 struct Body {
@@ -94,8 +94,8 @@ struct Body {
 struct Model {
   int sys = 0, n = 0, m = 0;
   double dt = 0;
-  // point mass
-  double wu = 0, wpT = 0, wvT = 0;
+  // point mass, Dubins car
+  double wu = 0, wpT = 0, wvT = 0, waT = 0;
   // bumps (point mass, planar arm)
   double bamp = 0, bsig = 1;
   int nb = 0;
@@ -123,6 +123,15 @@ static bool parse(int sys, const double* p, int np, Model& md) {
     if (md.nb < 0 || md.nb > 8 || np < 7 + 2 * md.nb) return false;
     for (int i = 0; i < md.nb; ++i) { md.bc[i][0] = p[5 + 2 * i]; md.bc[i][1] = p[6 + 2 * i]; }
     md.wpT = p[5 + 2 * md.nb]; md.wvT = p[6 + 2 * md.nb];
+    return true;
+  }
+  if (sys == SYS_DUBINS) {
+    if (np < 5) return false;
+    md.n = 5; md.m = 2;
+    md.dt = p[0]; md.wu = p[1]; md.bamp = p[2]; md.bsig = p[3]; md.nb = (int)p[4];
+    if (md.nb < 0 || md.nb > 8 || np < 8 + 2 * md.nb) return false;
+    for (int i = 0; i < md.nb; ++i) { md.bc[i][0] = p[5 + 2 * i]; md.bc[i][1] = p[6 + 2 * i]; }
+    md.wpT = p[5 + 2 * md.nb]; md.wvT = p[6 + 2 * md.nb]; md.waT = p[7 + 2 * md.nb];
     return true;
   }
   if (sys < SYS_PLANAR3 || sys > SYS_QUAD || np < 8) return false;
@@ -452,6 +461,15 @@ template <class S> static void step(const Model& md, const S* x, const S* u, S* 
     xn[3] = x[3] + md.dt * u[1];
     return;
   }
+  if (md.sys == SYS_DUBINS) {
+    // jerk-controlled Dubins car: (px, py, theta, v, a), u = (omega, jerk)
+    xn[0] = x[0] + md.dt * x[3] * cos(x[2]);
+    xn[1] = x[1] + md.dt * x[3] * sin(x[2]);
+    xn[2] = x[2] + md.dt * u[0];
+    xn[3] = x[3] + md.dt * x[4];
+    xn[4] = x[4] + md.dt * u[1];
+    return;
+  }
   const int N = md.N;
   const double h = md.dt / md.n_sub;
   std::vector<S> tau(N, S(0.0)), qdd(N), cur(x, x + 2 * N);
@@ -480,7 +498,7 @@ template <class S> static S bump(const Model& md, const S& px, const S& py) {
 
 template <class S> static S running_cost(const Model& md, const S* x, const S* u) {
   S l = S(0.0);
-  if (md.sys == SYS_PM) {
+  if (md.sys == SYS_PM || md.sys == SYS_DUBINS) {
     l = md.wu * (u[0] * u[0] + u[1] * u[1]) + bump(md, x[0], x[1]);
   } else if (md.sys == SYS_PLANAR3) {
     S ee[3];
@@ -502,6 +520,8 @@ template <class S> static S terminal_cost(const Model& md, const S* x) {
   S l = S(0.0);
   if (md.sys == SYS_PM) {
     l = md.wpT * (x[0] * x[0] + x[1] * x[1]) + md.wvT * (x[2] * x[2] + x[3] * x[3]);
+  } else if (md.sys == SYS_DUBINS) {
+    l = md.wpT * (x[0] * x[0] + x[1] * x[1]) + md.wvT * x[3] * x[3] + md.waT * x[4] * x[4];
   } else if (md.sys == SYS_PLANAR3 || md.sys == SYS_ARM7) {
     S ee[3];
     point_world(md, x, md.ee_body, md.ee_pt, ee);
@@ -986,14 +1006,14 @@ int oracle_cost_value(int sys, const double* p, int np, const double* x, const d
 int oracle_rnea(int sys, const double* p, int np, const double* q, const double* qd, const double* qdd, int grav,
                 int contact, double* tau) {
   Model md;
-  if (!parse(sys, p, np, md) || sys == SYS_PM) return -1;
+  if (!parse(sys, p, np, md) || sys == SYS_PM || sys == SYS_DUBINS) return -1;
   rnea(md, q, qd, qdd, grav != 0, contact != 0, tau);
   return 0;
 }
 
 int oracle_mass_matrix(int sys, const double* p, int np, const double* q, double* M) {
   Model md;
-  if (!parse(sys, p, np, md) || sys == SYS_PM) return -1;
+  if (!parse(sys, p, np, md) || sys == SYS_PM || sys == SYS_DUBINS) return -1;
   mass_matrix(md, q, M);
   return 0;
 }
@@ -1001,7 +1021,7 @@ int oracle_mass_matrix(int sys, const double* p, int np, const double* q, double
 int oracle_forward_dynamics(int sys, const double* p, int np, const double* q, const double* qd, const double* tau,
                             double* qdd) {
   Model md;
-  if (!parse(sys, p, np, md) || sys == SYS_PM) return -1;
+  if (!parse(sys, p, np, md) || sys == SYS_PM || sys == SYS_DUBINS) return -1;
   forward_dynamics(md, q, qd, tau, qdd);
   return 0;
 }
@@ -1011,7 +1031,7 @@ int oracle_forward_dynamics(int sys, const double* p, int np, const double* q, c
 int oracle_point_world(int sys, const double* p, int np, const double* q, int body, const double* pt, double* out,
                        double* E0out) {
   Model md;
-  if (!parse(sys, p, np, md) || sys == SYS_PM || body < 0 || body >= md.N) return -1;
+  if (!parse(sys, p, np, md) || sys == SYS_PM || sys == SYS_DUBINS || body < 0 || body >= md.N) return -1;
   point_world(md, q, body, pt, out);
   if (E0out) {
     std::vector<M3<double>> E0; std::vector<V3<double>> p0;

@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libto.so")
 
-TO_SYS_POINTMASS2D, TO_SYS_PLANAR3, TO_SYS_ARM7, TO_SYS_QUAD18 = 1, 2, 3, 4
+TO_SYS_POINTMASS2D, TO_SYS_PLANAR3, TO_SYS_ARM7, TO_SYS_QUAD18, TO_SYS_DUBINS = 1, 2, 3, 4, 5
 TO_FP64, TO_MIXED = 0, 1
 TO_OK, TO_ERR_ARG, TO_ERR_CUDA, TO_ERR_BUDGET, TO_ERR_TIMEOUT, TO_ERR_NOTREADY, TO_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 TO_ST_CONVERGED, TO_ST_MAX_ITER, TO_ST_LS_FAIL, TO_ST_NONFINITE, TO_ST_TIMEOUT, TO_ST_FLAG_REG = 1, 2, 3, 4, 5, 16

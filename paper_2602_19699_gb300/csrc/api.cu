@@ -24,6 +24,7 @@ const SysOps& pointmass_ops();
 const SysOps& planar3_ops();
 const SysOps& arm7_ops();
 const SysOps& quad_ops();
+const SysOps& dubins_ops();
 
 const SysOps* sys_ops(int sys) {
   switch (sys) {
@@ -31,6 +32,7 @@ const SysOps* sys_ops(int sys) {
     case TO_SYS_PLANAR3: return &planar3_ops();
     case TO_SYS_ARM7: return &arm7_ops();
     case TO_SYS_QUAD18: return &quad_ops();
+    case TO_SYS_DUBINS: return &dubins_ops();
     default: return nullptr;
   }
 }

@@ -1,0 +1,48 @@
+// Jerk-controlled Dubins car: parameter parsing and solver instantiation.
+#include <cmath>
+
+#include "launch.cuh"
+#include "sys_dubins.cuh"
+
+namespace to {
+
+static int parse_dubins(const double* p, size_t np, std::vector<unsigned char>& blob64,
+                        std::vector<unsigned char>& blob32, std::string& err) {
+  if (np < 5) { err = "dubins params: need at least 5 values"; return -1; }
+  DubinsParams<double> P{};
+  P.dt = p[0]; P.wu = p[1]; P.bamp = p[2]; P.bsig = p[3];
+  P.nb = (int)p[4];
+  if (P.nb < 0 || P.nb > 8 || np < (size_t)(8 + 2 * P.nb)) { err = "dubins params: bad bump count"; return -1; }
+  if (!(P.bsig > 0)) { err = "dubins params: bump sigma must be > 0"; return -1; }
+  for (int b = 0; b < P.nb; ++b) { P.bc[b][0] = p[5 + 2 * b]; P.bc[b][1] = p[6 + 2 * b]; }
+  P.wpT = p[5 + 2 * P.nb];
+  P.wvT = p[6 + 2 * P.nb];
+  P.waT = p[7 + 2 * P.nb];
+  to_blobs<DubinsParams>(P, blob64, blob32);
+  return 0;
+}
+
+typedef Dispatch<SysDubins, 8, 16, 32> DBDispatch;
+
+static SysOps make_ops() {
+  SysOps o{};
+  o.sys = 5;
+  fill_layout<SysDubins>(o);
+  o.n_groups = 3;
+  o.groups[0] = 8; o.groups[1] = 16; o.groups[2] = 32;
+  o.default_G = 8;
+  o.default_gpb[0] = 8; o.default_gpb[1] = 8;
+  o.accepts_actor = false;
+  o.parse = parse_dubins;
+  o.launch = DBDispatch::launch;
+  o.occupancy = DBDispatch::occupancy;
+  o.knot_costs = knot_costs_one<SysDubins>;
+  return o;
+}
+
+const SysOps& dubins_ops() {
+  static SysOps o = make_ops();
+  return o;
+}
+
+}  // namespace to

@@ -39,7 +39,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .workload import ARM7, PLANAR3, POINTMASS, QUAD
+from .workload import ARM7, DUBINS, PLANAR3, POINTMASS, QUAD
 
 
 def riccati_flops(n: int, m: int, refine: bool) -> int:
@@ -56,6 +56,9 @@ def riccati_flops(n: int, m: int, refine: bool) -> int:
 _SYSTEM = {
     POINTMASS: dict(primal=0, tangent=0, minv=0, costd=60, cost_step=40),
     PLANAR3: dict(primal=277, tangent=252, minv=24, costd=280, cost_step=314),
+    # Dubins car: closed-form A, B (sincos + 6), bump terms and 2x2 clip as
+    # the point mass, running cost + step with the heading's sincos
+    DUBINS: dict(primal=0, tangent=0, minv=0, costd=70, cost_step=55),
 }
 
 
@@ -89,6 +92,8 @@ def derivative_flops(sys: int, n: int, m: int, params=None) -> int:
     c = _SYSTEM[sys]
     if sys == POINTMASS:
         return c["costd"]
+    if sys == DUBINS:
+        return 8 + c["costd"]
     return c["primal"] + n * c["tangent"] + m * c["minv"] + c["costd"]
 
 

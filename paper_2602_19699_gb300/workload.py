@@ -19,6 +19,9 @@ manipulator, quadruped) at the sizes of the synthetic workloads:
 * ``ARM7`` (3): 7-DoF serial arm (axes z,y,z,y,z,y,z), n=14, m=7, T=200.
 * ``QUAD`` (4): floating base (6 virtual joints) + 4 legs x 3 joints,
   n=36, m=12, penalty-spring ground contact, actor-MLP warm start, T=100.
+* ``DUBINS`` (5): jerk-controlled Dubins car [px,py,theta,v,a], u=[omega,jerk],
+  explicit Euler dt=0.05, T=100, three Gaussian obstacle bumps, terminal
+  50|p|^2 + v^2 + a^2.
 """
 from __future__ import annotations
 
@@ -27,9 +30,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-POINTMASS, PLANAR3, ARM7, QUAD = 1, 2, 3, 4
-SYSTEM_NAMES = {POINTMASS: "pointmass2d", PLANAR3: "planar3", ARM7: "arm7", QUAD: "quad18"}
-NM = {POINTMASS: (4, 2), PLANAR3: (6, 3), ARM7: (14, 7), QUAD: (36, 12)}
+POINTMASS, PLANAR3, ARM7, QUAD, DUBINS = 1, 2, 3, 4, 5
+SYSTEM_NAMES = {POINTMASS: "pointmass2d", PLANAR3: "planar3", ARM7: "arm7", QUAD: "quad18", DUBINS: "dubins"}
+NM = {POINTMASS: (4, 2), PLANAR3: (6, 3), ARM7: (14, 7), QUAD: (36, 12), DUBINS: (5, 2)}
 
 # joint types of the rigid-body tree format
 RX, RY, RZ, PX, PY, PZ = 0, 1, 2, 3, 4, 5
@@ -108,6 +111,24 @@ def pointmass(seed: int = 0, n_bumps: int = 3, bump_amp: float = 5.0) -> Problem
     p[5 + 2 * n_bumps] = 50.0   # terminal position weight
     p[6 + 2 * n_bumps] = 1.0    # terminal velocity weight
     return Problem(POINTMASS, 4, 2, 0.05, p, meta={"centres": centres})
+
+
+def dubins(seed: int = 0, n_bumps: int = 3, bump_amp: float = 5.0) -> Problem:
+    """Jerk-controlled Dubins car with Gaussian obstacle bumps (the time state
+    of the paper's version is dropped: every solve starts at t = 0)."""
+    r = _rng(seed, 0)
+    centres = r.uniform(-1.0, 1.0, size=(n_bumps, 2))
+    p = np.zeros(5 + 2 * n_bumps + 3)
+    p[0] = 0.05          # dt
+    p[1] = 0.5e-2        # control weight
+    p[2] = bump_amp      # bump amplitude
+    p[3] = 0.1           # bump sigma
+    p[4] = n_bumps
+    p[5:5 + 2 * n_bumps] = centres.ravel()
+    p[5 + 2 * n_bumps] = 50.0   # terminal position weight
+    p[6 + 2 * n_bumps] = 1.0    # terminal speed weight
+    p[7 + 2 * n_bumps] = 1.0    # terminal acceleration weight
+    return Problem(DUBINS, 5, 2, 0.05, p, meta={"centres": centres})
 
 
 def planar3(seed: int = 0, n_bumps: int = 2, bump_amp: float = 5.0) -> Problem:
@@ -255,7 +276,7 @@ def actor_param_count(sizes=ACTOR_SIZES) -> int:
 
 
 def make_problem(sys: int, seed: int = 0, **kw) -> Problem:
-    return {POINTMASS: pointmass, PLANAR3: planar3, ARM7: arm7, QUAD: quad}[sys](seed, **kw)
+    return {POINTMASS: pointmass, PLANAR3: planar3, ARM7: arm7, QUAD: quad, DUBINS: dubins}[sys](seed, **kw)
 
 
 # --------------------------------------------------------------------------
@@ -281,6 +302,11 @@ def make_batch(prob: Problem, B: int, seed: int = 0, T: int | tuple | None = Non
         x0[:, 2] = prob.meta["z_nom"] + r.uniform(-0.05, 0.05, size=B)
         nominal = np.tile([0.0, th, -2.0 * th], 4)
         x0[:, 6:18] = nominal + r.uniform(-0.2, 0.2, size=(B, 12))
+        Td = 100
+    elif prob.sys == DUBINS:
+        # position in the obstacle field's square, any heading, at rest
+        x0[:, 0:2] = r.uniform(-2.0, 2.0, size=(B, 2))
+        x0[:, 2] = r.uniform(-math.pi, math.pi, size=B)
         Td = 100
     else:
         raise ValueError(prob.sys)

@@ -14,7 +14,7 @@ import pytest
 from paper_2602_19699_gb300 import workload as W
 
 
-@pytest.mark.parametrize("make", [W.pointmass, W.planar3, W.arm7])
+@pytest.mark.parametrize("make", [W.pointmass, W.planar3, W.arm7, W.dubins])
 def test_critic_targets_pins(oracle_mod, make):
     prob = make(seed=3)
     o = oracle_mod.Oracle.from_problem(prob)

@@ -17,7 +17,7 @@ def _rel(a, b):
     return np.abs(a - b).max() / max(1.0, np.abs(b).max())
 
 
-@pytest.mark.parametrize("sysid", [W.POINTMASS, W.PLANAR3, W.ARM7, W.QUAD])
+@pytest.mark.parametrize("sysid", [W.POINTMASS, W.PLANAR3, W.ARM7, W.QUAD, W.DUBINS])
 def test_dynamics_jacobians_match_central_differences(oracle_mod, sysid):
     prob = W.make_problem(sysid, seed=11)
     o = oracle_mod.Oracle.from_problem(prob)
@@ -39,7 +39,7 @@ def test_dynamics_jacobians_match_central_differences(oracle_mod, sysid):
         assert _rel(B, Bfd) < 1e-7
 
 
-@pytest.mark.parametrize("sysid", [W.POINTMASS, W.PLANAR3, W.ARM7, W.QUAD])
+@pytest.mark.parametrize("sysid", [W.POINTMASS, W.PLANAR3, W.ARM7, W.QUAD, W.DUBINS])
 @pytest.mark.parametrize("terminal", [False, True])
 def test_cost_gradient_and_hessian_match_central_differences(oracle_mod, sysid, terminal):
     prob = W.make_problem(sysid, seed=12)

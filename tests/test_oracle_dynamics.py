@@ -250,3 +250,29 @@ def test_quadruped_contact_force_direction(oracle_mod):
         fz += k * math.log1p(math.exp(-beta * z)) / beta
     assert fz > 0
     assert abs(-with_c[2] - fz) < 1e-9 * fz
+
+
+def test_dubins_closed_forms(oracle_mod):
+    """Explicit-Euler Dubins car: a constant turn rate at constant speed sums
+    a geometric series of headings (Sum_k cos(a + k d) = sin(K d / 2) /
+    sin(d / 2) cos(a + (K - 1) d / 2)); a constant jerk integrates twice to
+    v_K = v_0 + K dt a_0 + dt^2 j K (K - 1) / 2."""
+    prob = W.dubins(seed=1)
+    o = oracle_mod.Oracle.from_problem(prob)
+    dt = prob.params[0]
+    th0, v, om, K = 0.3, 1.7, 0.9, 40
+    x = np.array([0.2, -0.4, th0, v, 0.0])
+    for _ in range(K):
+        x = o.step(x, np.array([om, 0.0]))
+    d = dt * om
+    g = np.sin(K * d / 2) / np.sin(d / 2)
+    px = 0.2 + dt * v * g * np.cos(th0 + (K - 1) * d / 2)
+    py = -0.4 + dt * v * g * np.sin(th0 + (K - 1) * d / 2)
+    np.testing.assert_allclose(x[:3], [px, py, th0 + K * d], rtol=1e-12, atol=1e-12)
+    assert x[3] == pytest.approx(v, rel=1e-15)
+    a0, j = 0.3, -0.8
+    x = np.array([0.0, 0.0, 0.0, 0.5, a0])
+    for _ in range(K):
+        x = o.step(x, np.array([0.0, j]))
+    assert x[3] == pytest.approx(0.5 + K * dt * a0 + dt * dt * j * K * (K - 1) / 2, rel=1e-12)
+    assert x[4] == pytest.approx(a0 + K * dt * j, rel=1e-12)

@@ -76,7 +76,7 @@ def _numpy_clip(Q, eps):
     return 0.5 * (P + P.T)
 
 
-@pytest.mark.parametrize("sysid", [W.POINTMASS, W.PLANAR3, W.ARM7, W.QUAD])
+@pytest.mark.parametrize("sysid", [W.POINTMASS, W.PLANAR3, W.ARM7, W.QUAD, W.DUBINS])
 def test_riccati_step_equals_dense_lq_subproblem(oracle_mod, sysid):
     prob = W.make_problem(sysid, seed=21)
     o = oracle_mod.Oracle.from_problem(prob)
@@ -109,7 +109,7 @@ def test_riccati_step_equals_dense_lq_subproblem(oracle_mod, sysid):
     np.testing.assert_allclose(dU_r, dU, atol=1e-8 * max(1.0, np.abs(dU).max()))
 
 
-@pytest.mark.parametrize("sysid,B,T", [(W.POINTMASS, 6, 50), (W.PLANAR3, 3, 60), (W.ARM7, 2, 30), (W.QUAD, 1, 20)])
+@pytest.mark.parametrize("sysid,B,T", [(W.POINTMASS, 6, 50), (W.PLANAR3, 3, 60), (W.ARM7, 2, 30), (W.QUAD, 1, 20), (W.DUBINS, 6, 60)])
 def test_cost_strictly_decreases_and_line_search_rule(oracle_mod, sysid, B, T):
     prob = W.make_problem(sysid, seed=31)
     o = oracle_mod.Oracle.from_problem(prob)
