@@ -155,6 +155,7 @@ struct Work {
   R xl[n];               // low parts of x_k (float32 rollouts)
   R K[m * n];            // gains K_k, k_k (adjacent)
   R kf[m];
+  R sx[Sys::template Scratch<R>::elems];   // the system's derivative scratch (rigid trees: per-substep primal)
   int flag;              // Cholesky: 0 ok, 1 regularised, 2 failed
   int sel;
   int wslot;             // slot of the accepted line-search candidate
@@ -358,7 +359,9 @@ struct Solver {
       }
     }
     // dynamics Jacobians and clipped running-cost derivatives
-    if (act) Sys::template derivs<R, G>(P, g, w.xk, w.uk, eps, w.A, w.Bm, w.lxx, w.lx, w.luu, w.lu, w.VA);
+    // (a system whose derivative step holds group barriers has groups of a
+    // whole warp or CTA, so act is uniform over every barrier's scope)
+    if (act) Sys::template derivs<R, G>(P, g, w.xk, w.uk, eps, w.A, w.Bm, w.lxx, w.lx, w.luu, w.lu, w.sx);
     g.sync();
     TO_TICK(1);
     // V A and V B

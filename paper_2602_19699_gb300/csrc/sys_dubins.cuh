@@ -28,6 +28,7 @@ struct SysDubins {
   static constexpr int n = 5, m = 2;
   static constexpr bool kActor = false;
   template <class R> using ParamsT = DubinsParams<R>;
+  template <class R> struct Scratch { static constexpr int elems = 1; };
 
   template <class R>
   TO_DEV static void step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {

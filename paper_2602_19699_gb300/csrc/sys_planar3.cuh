@@ -44,6 +44,7 @@ struct SysPlanar3 {
   static constexpr int n = 6, m = 3;
   static constexpr bool kActor = false;
   template <class R> using ParamsT = Planar3Params<R>;
+  template <class R> struct Scratch { static constexpr int elems = 1; };
 
   // absolute link angles, link and centre-of-mass vectors, joint positions
   template <class R>

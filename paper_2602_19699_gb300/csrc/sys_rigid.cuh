@@ -13,7 +13,10 @@
 // coordinate, or a control) through the substeps:
 //   dqdd = M^{-1} (dtau - d ID(q, qd, qdd) / d(q, qd) . (dq, dqd)),
 // with the directional derivative of the inverse dynamics (qdd held fixed)
-// from a dual-number pass of the same Newton-Euler code.
+// from a hand-written tangent pass over per-body primal quantities that one
+// lane stores in shared memory per substep (the product rule of the
+// Newton-Euler recursion; a dual-number pass of the same code serves the
+// arm's nested terminal Hessian).
 #pragma once
 #include "common.cuh"
 
@@ -592,39 +595,358 @@ struct SysRigid {
     }
   }
 
-  // Columns of [A | B]: lane c < n propagates the tangent e_c of the state,
-  // lane n + j the tangent of control j, through the n_sub substeps.  The
-  // last lane also writes the (separable) running-cost derivatives.
+  // ---- group-shared primal of one substep and the per-lane tangent pass ----
+  static constexpr int NF = (KIND == RK_QUAD) ? 4 : 1;
+  // Per-body quantities of the Newton-Euler pass at (q, qd, qdd), the mass
+  // matrix factor and the contact terms: computed once per substep by one
+  // lane into shared memory, read by every tangent lane.
+  template <class R>
+  struct Prim {
+    R q[N], qd[N], qdd[N], tau[N], tin[N];
+    R L[N * N];
+    R E[N][9], r[N][3];
+    R vw[N][3], vv[N][3];       // body velocity
+    R Epw[N][3], Ept[N][3];     // E pw and E (pv - r x pw): the parent's velocity in body coordinates
+    R Epa[N][3], Epb[N][3];     // E paw and E (pav - r x paw): the same for the acceleration
+    R aw[N][3];                 // body angular acceleration
+    R hn[N][3], hf[N][3];       // I v
+    R fn[N][3], ff[N][3];       // body force as sent to the parent (children and contact included)
+    R E0[KIND == RK_QUAD ? N : 1][9], p0[KIND == RK_QUAD ? N : 1][3];
+    R wpt[NF][3], F[NF][3], vb[NF][3], vwld[NF][3], gate[NF];
+  };
+  // the group's shared-memory scratch (the solver reserves it in its work area)
+  template <class R>
+  struct Scratch {
+    static constexpr int elems = (int)((sizeof(Prim<R>) + sizeof(R) - 1) / sizeof(R));
+  };
+
+  // y += a x b
+  template <class S> TO_DEV static void cross_acc(const S* a, const S* b, S* y) {
+    y[0] += a[1] * b[2] - a[2] * b[1];
+    y[1] += a[2] * b[0] - a[0] * b[2];
+    y[2] += a[0] * b[1] - a[1] * b[0];
+  }
+  // y -= s (e_ax x z): the change of E x under dq about joint axis ax
+  template <class S> TO_DEV static void rot_tangent(int ax, S s, const S* z, S* y) {
+    if (ax == 0) { y[1] += s * z[2]; y[2] -= s * z[1]; }
+    else if (ax == 1) { y[0] -= s * z[2]; y[2] += s * z[0]; }
+    else { y[0] += s * z[1]; y[1] -= s * z[0]; }
+  }
+  // e_ax x z
+  template <class S> TO_DEV static void axis_cross(int ax, const S* z, S* y) {
+    if (ax == 0) { y[0] = S(0); y[1] = -z[2]; y[2] = z[1]; }
+    else if (ax == 1) { y[0] = z[2]; y[1] = S(0); y[2] = -z[0]; }
+    else { y[0] = -z[1]; y[1] = z[0]; y[2] = S(0); }
+  }
+
+  // Newton-Euler at the substep's (q, qd, qdd) in pr (gravity, and contact for
+  // the quadruped), keeping every per-body quantity the tangent pass needs.
+  template <class R>
+  TO_DEV static void rnea_store(const ParamsT<R>& P, Prim<R>& pr) {
+    R (*aw)[3] = pr.aw;
+    R av[N][3];
+    for (int i = 0; i < N; ++i) {
+      joint_transform(P, i, pr.q[i], pr.E[i], pr.r[i]);
+      const int pa = P.parent[i];
+      R pw[3], pv[3], paw[3], pav[3];
+      for (int k = 0; k < 3; ++k) {
+        pw[k] = pa < 0 ? R(0) : pr.vw[pa][k];
+        pv[k] = pa < 0 ? R(0) : pr.vv[pa][k];
+        paw[k] = pa < 0 ? R(0) : aw[pa][k];
+        pav[k] = pa < 0 ? -P.g[k] : av[pa][k];
+      }
+      const R* E = pr.E[i];
+      const R* r = pr.r[i];
+      R t[3], rw[3];
+      cross(r, pw, rw);
+      for (int k = 0; k < 3; ++k) t[k] = pv[k] - rw[k];
+      mv(E, pw, pr.Epw[i]);
+      mv(E, t, pr.Ept[i]);
+      cross(r, paw, rw);
+      for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
+      mv(E, paw, pr.Epa[i]);
+      mv(E, t, pr.Epb[i]);
+      const int jt = P.jtype[i];
+      R sw[3] = {R(0), R(0), R(0)}, sv[3] = {R(0), R(0), R(0)};
+      if (jt <= 2) sw[jt] = pr.qd[i]; else sv[jt - 3] = pr.qd[i];
+      for (int k = 0; k < 3; ++k) { pr.vw[i][k] = pr.Epw[i][k] + sw[k]; pr.vv[i][k] = pr.Ept[i][k] + sv[k]; }
+      for (int k = 0; k < 3; ++k) { aw[i][k] = pr.Epa[i][k]; av[i][k] = pr.Epb[i][k]; }
+      cross_acc(pr.vw[i], sw, aw[i]);
+      cross_acc(pr.vw[i], sv, av[i]);
+      cross_acc(pr.vv[i], sw, av[i]);
+      if (jt <= 2) aw[i][jt] += pr.qdd[i]; else av[i][jt - 3] += pr.qdd[i];
+      R In[3], If[3];
+      inertia_mul(P, i, aw[i], av[i], In, If);
+      inertia_mul(P, i, pr.vw[i], pr.vv[i], pr.hn[i], pr.hf[i]);
+      for (int k = 0; k < 3; ++k) { pr.fn[i][k] = In[k]; pr.ff[i][k] = If[k]; }
+      cross_acc(pr.vw[i], pr.hn[i], pr.fn[i]);
+      cross_acc(pr.vv[i], pr.hf[i], pr.fn[i]);
+      cross_acc(pr.vw[i], pr.hf[i], pr.ff[i]);
+      if (KIND == RK_QUAD) {
+        if (pa < 0) {
+          for (int k = 0; k < 9; ++k) pr.E0[i][k] = E[k];
+          for (int k = 0; k < 3; ++k) pr.p0[i][k] = r[k];
+        } else {
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+              pr.E0[i][a * 3 + b] = E[a * 3 + 0] * pr.E0[pa][b] + E[a * 3 + 1] * pr.E0[pa][3 + b] + E[a * 3 + 2] * pr.E0[pa][6 + b];
+          R wr[3];
+          mtv(pr.E0[pa], r, wr);
+          for (int k = 0; k < 3; ++k) pr.p0[i][k] = pr.p0[pa][k] + wr[k];
+        }
+      }
+    }
+    if (KIND == RK_QUAD) {
+      for (int ft = 0; ft < P.nfeet; ++ft) {
+        const int bi = P.foot_body[ft];
+        const R pt[3] = {P.foot_pt[ft][0], P.foot_pt[ft][1], P.foot_pt[ft][2]};
+        mtv(pr.E0[bi], pt, pr.wpt[ft]);
+        R wxp[3];
+        cross(pr.vw[bi], pt, wxp);
+        for (int k = 0; k < 3; ++k) pr.vb[ft][k] = pr.vv[bi][k] + wxp[k];
+        mtv(pr.E0[bi], pr.vb[ft], pr.vwld[ft]);
+        const R bz = P.beta * (pr.p0[bi][2] + pr.wpt[ft][2]);
+        R sp, gate;
+        if (bz >= R(0)) {
+          const R e = dexp(-bz);
+          sp = (R(1) / P.beta) * dlog1p(e);
+          gate = e / (R(1) + e);
+        } else {
+          const R e = dexp(bz);
+          sp = (R(1) / P.beta) * (dlog1p(e) - bz);
+          gate = R(1) / (R(1) + e);
+        }
+        pr.gate[ft] = gate;
+        R* F = pr.F[ft];
+        F[0] = -(P.dc * (gate * pr.vwld[ft][0]));
+        F[1] = -(P.dc * (gate * pr.vwld[ft][1]));
+        F[2] = P.kc * sp - P.dc * (gate * pr.vwld[ft][2]);
+        R mw[3], mb[3], fb[3];
+        cross(pr.wpt[ft], F, mw);
+        mv(pr.E0[bi], mw, mb);
+        mv(pr.E0[bi], F, fb);
+        for (int k = 0; k < 3; ++k) { pr.fn[bi][k] -= mb[k]; pr.ff[bi][k] -= fb[k]; }
+      }
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      const int jt = P.jtype[i];
+      pr.tau[i] = jt <= 2 ? pr.fn[i][jt] : pr.ff[i][jt - 3];
+      const int pa = P.parent[i];
+      if (pa >= 0) {
+        R en[3], ef[3], rf[3];
+        mtv(pr.E[i], pr.fn[i], en);
+        mtv(pr.E[i], pr.ff[i], ef);
+        cross(pr.r[i], ef, rf);
+        for (int k = 0; k < 3; ++k) { pr.fn[pa][k] += en[k] + rf[k]; pr.ff[pa][k] += ef[k]; }
+      }
+    }
+  }
+
+  // Directional derivative of the inverse dynamics along (dq, dqd) at the
+  // stored substep (qdd held fixed): the product rule through the forward
+  // recursion (velocities, accelerations, body forces, world poses and
+  // contact) and the backward force recursion.  Only the tangents live in
+  // the lane's own arrays.
+  template <class R>
+  TO_DEV static void rnea_tangent(const ParamsT<R>& P, const Prim<R>& pr, const R* dq, const R* dqd, R* dtau) {
+    R dvw[N][3], dvv[N][3], daw[N][3], dav[N][3], dfn[N][3], dff[N][3];
+    R dE0[KIND == RK_QUAD ? N : 1][9], dp0[KIND == RK_QUAD ? N : 1][3];
+    for (int i = 0; i < N; ++i) {
+      const int pa = P.parent[i];
+      const int jt = P.jtype[i];
+      const bool rev = jt <= 2;
+      const int ax = rev ? jt : jt - 3;
+      const R sq = rev ? dq[i] : R(0);          // rotation tangent
+      R dr[3] = {R(0), R(0), R(0)};
+      if (!rev) dr[ax] = dq[i];
+      const R* E = pr.E[i];
+      const R* r = pr.r[i];
+      R dpw[3], dpv[3], dpaw[3], dpav[3], pw[3], paw[3];
+      for (int k = 0; k < 3; ++k) {
+        dpw[k] = pa < 0 ? R(0) : dvw[pa][k];
+        dpv[k] = pa < 0 ? R(0) : dvv[pa][k];
+        dpaw[k] = pa < 0 ? R(0) : daw[pa][k];
+        dpav[k] = pa < 0 ? R(0) : dav[pa][k];
+        pw[k] = pa < 0 ? R(0) : pr.vw[pa][k];
+        paw[k] = pa < 0 ? R(0) : pr.aw[pa][k];
+      }
+      // velocity
+      R t[3], u3[3];
+      mv(E, dpw, dvw[i]);
+      rot_tangent(ax, rev ? sq : R(0), pr.Epw[i], dvw[i]);
+      for (int k = 0; k < 3; ++k) t[k] = dpv[k];
+      cross(r, dpw, u3);
+      for (int k = 0; k < 3; ++k) t[k] -= u3[k];
+      cross(dr, pw, u3);
+      for (int k = 0; k < 3; ++k) t[k] -= u3[k];
+      mv(E, t, dvv[i]);
+      rot_tangent(ax, rev ? sq : R(0), pr.Ept[i], dvv[i]);
+      R sw[3] = {R(0), R(0), R(0)}, sv[3] = {R(0), R(0), R(0)}, dsw[3] = {R(0), R(0), R(0)}, dsv[3] = {R(0), R(0), R(0)};
+      if (rev) { sw[ax] = pr.qd[i]; dsw[ax] = dqd[i]; } else { sv[ax] = pr.qd[i]; dsv[ax] = dqd[i]; }
+      for (int k = 0; k < 3; ++k) { dvw[i][k] += dsw[k]; dvv[i][k] += dsv[k]; }
+      // acceleration (qdd fixed)
+      mv(E, dpaw, daw[i]);
+      rot_tangent(ax, rev ? sq : R(0), pr.Epa[i], daw[i]);
+      for (int k = 0; k < 3; ++k) t[k] = dpav[k];
+      cross(r, dpaw, u3);
+      for (int k = 0; k < 3; ++k) t[k] -= u3[k];
+      cross(dr, paw, u3);
+      for (int k = 0; k < 3; ++k) t[k] -= u3[k];
+      mv(E, t, dav[i]);
+      rot_tangent(ax, rev ? sq : R(0), pr.Epb[i], dav[i]);
+      cross_acc(dvw[i], sw, daw[i]);
+      cross_acc(pr.vw[i], dsw, daw[i]);
+      cross_acc(dvw[i], sv, dav[i]);
+      cross_acc(pr.vw[i], dsv, dav[i]);
+      cross_acc(dvv[i], sw, dav[i]);
+      cross_acc(pr.vv[i], dsw, dav[i]);
+      // body force
+      R dIn[3], dIf[3], dhn[3], dhf[3];
+      inertia_mul(P, i, daw[i], dav[i], dIn, dIf);
+      inertia_mul(P, i, dvw[i], dvv[i], dhn, dhf);
+      for (int k = 0; k < 3; ++k) { dfn[i][k] = dIn[k]; dff[i][k] = dIf[k]; }
+      cross_acc(dvw[i], pr.hn[i], dfn[i]);
+      cross_acc(pr.vw[i], dhn, dfn[i]);
+      cross_acc(dvv[i], pr.hf[i], dfn[i]);
+      cross_acc(pr.vv[i], dhf, dfn[i]);
+      cross_acc(dvw[i], pr.hf[i], dff[i]);
+      cross_acc(pr.vw[i], dhf, dff[i]);
+      if (KIND == RK_QUAD) {
+        // world pose: dE0_i = dE_i E0_p + E_i dE0_p, dp0_i = dp0_p + dE0_p^T r + E0_p^T dr
+        const R* E0 = pr.E0[i];
+        if (pa < 0) {
+          for (int k = 0; k < 9; ++k) dE0[i][k] = R(0);
+          for (int k = 0; k < 3; ++k) dp0[i][k] = dr[k];
+        } else {
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+              dE0[i][a * 3 + b] = E[a * 3 + 0] * dE0[pa][b] + E[a * 3 + 1] * dE0[pa][3 + b] + E[a * 3 + 2] * dE0[pa][6 + b];
+          R w1[3], w2[3];
+          mtv(dE0[pa], r, w1);
+          mtv(pr.E0[pa], dr, w2);
+          for (int k = 0; k < 3; ++k) dp0[i][k] = dp0[pa][k] + w1[k] + w2[k];
+        }
+        if (rev) {
+          // column b of E0_i turns with the joint: -dq (e_ax x column)
+          for (int b = 0; b < 3; ++b) {
+            const R col[3] = {E0[0 * 3 + b], E0[1 * 3 + b], E0[2 * 3 + b]};
+            R y[3] = {R(0), R(0), R(0)};
+            rot_tangent(ax, sq, col, y);
+            for (int a = 0; a < 3; ++a) dE0[i][a * 3 + b] += y[a];
+          }
+        }
+      }
+    }
+    if (KIND == RK_QUAD) {
+      for (int ft = 0; ft < P.nfeet; ++ft) {
+        const int bi = P.foot_body[ft];
+        const R pt[3] = {P.foot_pt[ft][0], P.foot_pt[ft][1], P.foot_pt[ft][2]};
+        const R* E0 = pr.E0[bi];
+        R dwpt[3], dvb[3], dvwld[3], w1[3];
+        mtv(dE0[bi], pt, dwpt);
+        const R dz = dp0[bi][2] + dwpt[2];
+        cross(dvw[bi], pt, w1);
+        for (int k = 0; k < 3; ++k) dvb[k] = dvv[bi][k] + w1[k];
+        mtv(dE0[bi], pr.vb[ft], dvwld);
+        mtv(E0, dvb, w1);
+        for (int k = 0; k < 3; ++k) dvwld[k] += w1[k];
+        const R gate = pr.gate[ft];
+        const R dgate = -P.beta * gate * (R(1) - gate) * dz;
+        const R dsp = -gate * dz;
+        R dF[3];
+        dF[0] = -P.dc * (dgate * pr.vwld[ft][0] + gate * dvwld[0]);
+        dF[1] = -P.dc * (dgate * pr.vwld[ft][1] + gate * dvwld[1]);
+        dF[2] = P.kc * dsp - P.dc * (dgate * pr.vwld[ft][2] + gate * dvwld[2]);
+        R mw[3], dmw[3] = {R(0), R(0), R(0)}, dmb[3], dfb[3];
+        cross(pr.wpt[ft], pr.F[ft], mw);
+        cross_acc(dwpt, pr.F[ft], dmw);
+        cross_acc(pr.wpt[ft], dF, dmw);
+        mv(dE0[bi], mw, dmb);
+        mv(E0, dmw, w1);
+        for (int k = 0; k < 3; ++k) dmb[k] += w1[k];
+        mv(dE0[bi], pr.F[ft], dfb);
+        mv(E0, dF, w1);
+        for (int k = 0; k < 3; ++k) dfb[k] += w1[k];
+        for (int k = 0; k < 3; ++k) { dfn[bi][k] -= dmb[k]; dff[bi][k] -= dfb[k]; }
+      }
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      const int jt = P.jtype[i];
+      const bool rev = jt <= 2;
+      const int ax = rev ? jt : jt - 3;
+      dtau[i] = rev ? dfn[i][ax] : dff[i][ax];
+      const int pa = P.parent[i];
+      if (pa >= 0) {
+        // d(E^T y) = E^T dy + dq E^T (e_ax x y) for a revolute joint
+        const R* E = pr.E[i];
+        R yn[3], yf[3], den[3], def[3], w1[3];
+        for (int k = 0; k < 3; ++k) { yn[k] = dfn[i][k]; yf[k] = dff[i][k]; }
+        if (rev) {
+          axis_cross(ax, pr.fn[i], w1);
+          for (int k = 0; k < 3; ++k) yn[k] += dq[i] * w1[k];
+          axis_cross(ax, pr.ff[i], w1);
+          for (int k = 0; k < 3; ++k) yf[k] += dq[i] * w1[k];
+        }
+        mtv(E, yn, den);
+        mtv(E, yf, def);
+        R ef[3], dr[3] = {R(0), R(0), R(0)};
+        if (!rev) dr[ax] = dq[i];
+        mtv(E, pr.ff[i], ef);
+        cross_acc(dr, ef, den);
+        cross_acc(pr.r[i], def, den);
+        for (int k = 0; k < 3; ++k) { dfn[pa][k] += den[k]; dff[pa][k] += def[k]; }
+      }
+    }
+  }
+
+  // Columns of [A | B]: lane c < n carries the tangent e_c of the state,
+  // lane n + j the tangent of control j, through the n_sub substeps.  Per
+  // substep, lane 0 evaluates the primal once (acceleration by the
+  // composite-rigid-body mass matrix, then the Newton-Euler quantities at
+  // that acceleration) into the group's shared scratch; every direction lane
+  // then runs only the tangent pass against it:
+  //   dqdd = M^{-1} (dtau - dID(q, qd, qdd)[dq, dqd]),
+  // and integrates its tangent like the state.  The last lane also writes
+  // the (separable) running-cost derivatives.
   template <class R, int G>
   TO_DEV static void derivs(const ParamsT<R>& P, const Group<G>& g, const R* x, const R* u, R eps, R* A, R* B,
-                            R* lxx, R* lx, R* luu, R* lu, R*) {
+                            R* lxx, R* lx, R* luu, R* lu, R* scratch) {
     static_assert(G >= n + m, "one lane per tangent direction");
+    Prim<R>& pr = *reinterpret_cast<Prim<R>*>(scratch);
     const int c = g.lane;
-    if (c < n + m) {
-      R q[N], qd[N], tau[N], dq[N], dqd[N];
-      for (int i = 0; i < N; ++i) {
-        q[i] = x[i]; qd[i] = x[N + i]; tau[i] = i < A0 ? R(0) : u[i - A0];
-        dq[i] = (c == i) ? R(1) : R(0);
-        dqd[i] = (c == N + i) ? R(1) : R(0);
+    const bool dir = c < n + m;
+    R dq[N], dqd[N];
+    for (int i = 0; i < N; ++i) {
+      dq[i] = (c == i) ? R(1) : R(0);
+      dqd[i] = (c == N + i) ? R(1) : R(0);
+    }
+    if (c == 0)
+      for (int i = 0; i < N; ++i) { pr.q[i] = x[i]; pr.qd[i] = x[N + i]; pr.tin[i] = i < A0 ? R(0) : u[i - A0]; }
+    const R h = P.dt / (R)P.n_sub;
+    for (int s = 0; s < P.n_sub; ++s) {
+      if (c == 0) {
+        accel(P, pr.q, pr.qd, pr.tin, pr.qdd, pr.L);
+        rnea_store(P, pr);
       }
-      const R h = P.dt / (R)P.n_sub;
-      for (int s = 0; s < P.n_sub; ++s) {
-        R qdd[N], L[N * N];
-        accel(P, q, qd, tau, qdd, L);
-        // directional derivative of ID at fixed qdd
-        Dl<R> Dq[N], Dqd[N], Dqdd[N], Dtau[N];
-        for (int i = 0; i < N; ++i) { Dq[i] = Dl<R>(q[i], dq[i]); Dqd[i] = Dl<R>(qd[i], dqd[i]); Dqdd[i] = Dl<R>(qdd[i], R(0)); }
-        rnea<R, Dl<R>>(P, Dq, Dqd, Dqdd, true, KIND == RK_QUAD, Dtau);
-        R rhs[N], dqdd[N];
-        for (int i = 0; i < N; ++i) rhs[i] = ((c >= n && i == A0 + (c - n)) ? R(1) : R(0)) - Dtau[i].d;
-        chol_solve(L, rhs, dqdd);
+      g.sync();
+      if (dir) {
+        R dtau[N], rhs[N], dqdd[N];
+        rnea_tangent(P, pr, dq, dqd, dtau);
+        for (int i = 0; i < N; ++i) rhs[i] = ((c >= n && i == A0 + (c - n)) ? R(1) : R(0)) - dtau[i];
+        chol_solve(pr.L, rhs, dqdd);
         for (int i = 0; i < N; ++i) {
-          qd[i] = qd[i] + h * qdd[i];
-          q[i] = q[i] + h * qd[i];
           dqd[i] = dqd[i] + h * dqdd[i];
           dq[i] = dq[i] + h * dqd[i];
         }
       }
+      g.sync();
+      if (c == 0)
+        for (int i = 0; i < N; ++i) {
+          pr.qd[i] = pr.qd[i] + h * pr.qdd[i];
+          pr.q[i] = pr.q[i] + h * pr.qd[i];
+        }
+    }
+    if (dir) {
       if (c < n) {
         for (int i = 0; i < N; ++i) { A[i * n + c] = dq[i]; A[(N + i) * n + c] = dqd[i]; }
       } else {
