@@ -42,7 +42,7 @@ const SysOps* sys_ops(int sys);
 constexpr int kMaxCtaThreads = 256;
 
 template <class Sys, class R, int G>
-__global__ void __launch_bounds__(kMaxCtaThreads) ilqr_kernel(SolveArgs a) {
+__global__ void __launch_bounds__(kMaxCtaThreads, 1) ilqr_kernel(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Solver<Sys, R, G>::run(a, smem_raw);
 }

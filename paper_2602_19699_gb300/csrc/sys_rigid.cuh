@@ -128,6 +128,32 @@ struct SysRigid {
     y[0] = y0; y[1] = y1; y[2] = y2;
   }
 
+  // y = E x and y = E^T x for a joint transform: a rotation about the joint's
+  // coordinate axis (4 nonzeros besides the unit entry) or the identity
+  // (prismatic); the joint type is the same on every lane at a given body.
+  // The sparse form pays in float64 (each FP64 instruction is costly on this
+  // part); in float32 the branch-free dense product measured faster.
+  template <class S> TO_DEV static void jmv(int jt, const S* E, const S* x, S* y) {
+    if constexpr (sizeof(S) == 4) { mv(E, x, y); return; }
+    const S x0 = x[0], x1 = x[1], x2 = x[2];
+    switch (jt) {
+      case 0: { const S c = E[4], s = E[5]; y[0] = x0; y[1] = c * x1 + s * x2; y[2] = c * x2 - s * x1; break; }
+      case 1: { const S c = E[0], s = E[6]; y[0] = c * x0 - s * x2; y[1] = x1; y[2] = c * x2 + s * x0; break; }
+      case 2: { const S c = E[0], s = E[1]; y[0] = c * x0 + s * x1; y[1] = c * x1 - s * x0; y[2] = x2; break; }
+      default: y[0] = x0; y[1] = x1; y[2] = x2;
+    }
+  }
+  template <class S> TO_DEV static void jmtv(int jt, const S* E, const S* x, S* y) {
+    if constexpr (sizeof(S) == 4) { mtv(E, x, y); return; }
+    const S x0 = x[0], x1 = x[1], x2 = x[2];
+    switch (jt) {
+      case 0: { const S c = E[4], s = E[5]; y[0] = x0; y[1] = c * x1 - s * x2; y[2] = c * x2 + s * x1; break; }
+      case 1: { const S c = E[0], s = E[6]; y[0] = c * x0 + s * x2; y[1] = x1; y[2] = c * x2 - s * x0; break; }
+      case 2: { const S c = E[0], s = E[1]; y[0] = c * x0 - s * x1; y[1] = c * x1 + s * x0; y[2] = x2; break; }
+      default: y[0] = x0; y[1] = x1; y[2] = x2;
+    }
+  }
+
   // Plucker transform of joint i: E maps parent coordinates to body
   // coordinates (a rotation by q about the joint axis, or identity), r is the
   // body origin in parent coordinates
@@ -223,13 +249,13 @@ struct SysRigid {
       cross(r[i], pw, rw);
 #pragma unroll
       for (int k = 0; k < 3; ++k) t[k] = pv[k] - rw[k];
-      mv(E[i], pw, vw[i]);
-      mv(E[i], t, vv[i]);
+      jmv(P.jtype[i], E[i], pw, vw[i]);
+      jmv(P.jtype[i], E[i], t, vv[i]);
       cross(r[i], paw, rw);
 #pragma unroll
       for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
-      mv(E[i], paw, aw);
-      mv(E[i], t, av);
+      jmv(P.jtype[i], E[i], paw, aw);
+      jmv(P.jtype[i], E[i], t, av);
       // joint motion S qd, S qdd; velocity-product term v x (S qd)
       const int jt = P.jtype[i];
       S sw[3] = {S(R(0)), S(R(0)), S(R(0))}, sv[3] = {S(R(0)), S(R(0)), S(R(0))};
@@ -319,8 +345,8 @@ struct SysRigid {
       if (pa >= 0) {
         // X^T f = (E^T n + r x E^T f, E^T f)
         S en[3], ef[3], rf[3];
-        mtv(E[i], fn[i], en);
-        mtv(E[i], ff[i], ef);
+        jmtv(jt, E[i], fn[i], en);
+        jmtv(jt, E[i], ff[i], ef);
         cross(r[i], ef, rf);
 #pragma unroll
         for (int k = 0; k < 3; ++k) { fn[pa][k] = fn[pa][k] + en[k] + rf[k]; ff[pa][k] = ff[pa][k] + ef[k]; }
@@ -330,7 +356,7 @@ struct SysRigid {
 
   // Joint-space mass matrix by the composite-rigid-body algorithm
   // (Featherstone 2008, Sec. 6.2), written into the lower triangle of L and
-  // Cholesky-factored in place with reciprocal pivots.  A subtree's composite
+  // factored in place as M = L^T L along the tree (reciprocal pivots).  A subtree's composite
   // inertia is kept about its root body's origin, in that body's coordinates,
   // as (mass, first moment h = mass * com, rotational inertia about the
   // origin); moving it to the parent frame rotates it and applies the
@@ -358,7 +384,7 @@ struct SysRigid {
       const R mi = cm[i];
       // h_A = E^T h (parent coordinates, about the child origin)
       R hA[3];
-      mtv(e, ch[i], hA);
+      jmtv(P.jtype[i], e, ch[i], hA);
       // I_A = E^T I E
       const R I3[9] = {cI[i][0], cI[i][3], cI[i][4], cI[i][3], cI[i][1], cI[i][5], cI[i][4], cI[i][5], cI[i][2]};
       R T[9];   // I E
@@ -383,8 +409,7 @@ struct SysRigid {
       for (int k = 0; k < 3; ++k) ch[pa][k] += hA[k] + mi * rr[k];
       cm[pa] += mi;
     }
-    // entries of bodies on different branches stay zero
-    for (int i = 0; i < N * N; ++i) L[i] = R(0);
+    // only (body, ancestor) entries are formed and read: the others are zero
     for (int i = 0; i < N; ++i) {
       // F = Ic_i S_i: revolute about axis a: (I e_a, e_a x h); prismatic along a: (h x e_a, m e_a)
       R fn[3], ff[3];
@@ -410,8 +435,8 @@ struct SysRigid {
       while (P.parent[j] >= 0) {
         // force to the parent frame: f_p = E^T f, n_p = E^T n + r x f_p
         R en[3], ef[3], rf[3];
-        mtv(E[j], fn, en);
-        mtv(E[j], ff, ef);
+        jmtv(P.jtype[j], E[j], fn, en);
+        jmtv(P.jtype[j], E[j], ff, ef);
         cross(r[j], ef, rf);
 #pragma unroll
         for (int k = 0; k < 3; ++k) { fn[k] = en[k] + rf[k]; ff[k] = ef[k]; }
@@ -420,30 +445,33 @@ struct SysRigid {
         L[i * N + j] = jj <= 2 ? fn[jj] : ff[jj - 3];
       }
     }
-    for (int j = 0; j < N; ++j) {
-      R s = L[j * N + j];
-      for (int k = 0; k < j; ++k) s -= L[j * N + k] * L[j * N + k];
-      const R rr = rsqrt_(s);
-      L[j * N + j] = rr;
-      for (int i = j + 1; i < N; ++i) {
-        R t = L[i * N + j];
-        for (int k = 0; k < j; ++k) t -= L[i * N + k] * L[j * N + k];
-        L[i * N + j] = t * rr;
+    // M = L^T L with L lower triangular and the tree's sparsity (Featherstone
+    // 2008, Sec. 6.5): eliminating from the last body up touches only
+    // (body, ancestor) pairs, so nothing fills in; 1 / L_kk on the diagonal
+    for (int k = N - 1; k >= 0; --k) {
+      const R rk = rsqrt_(L[k * N + k]);
+      L[k * N + k] = rk;
+      for (int i = P.parent[k]; i >= 0; i = P.parent[i]) L[k * N + i] *= rk;
+      for (int i = P.parent[k]; i >= 0; i = P.parent[i]) {
+        const R lki = L[k * N + i];
+        for (int j = i; j >= 0; j = P.parent[j]) L[i * N + j] -= lki * L[k * N + j];
       }
     }
   }
+  // x = M^{-1} b with M = L^T L from mass_chol: L^T y = b from the leaves up,
+  // then L x = y from the root down, each along the ancestor chains
   template <class R>
-  TO_DEV static void chol_solve(const R* L, const R* b, R* x) {
+  TO_DEV static void chol_solve(const ParamsT<R>& P, const R* L, const R* b, R* x) {
     R y[N];
-    for (int i = 0; i < N; ++i) {
-      R t = b[i];
-      for (int k = 0; k < i; ++k) t -= L[i * N + k] * y[k];
-      y[i] = t * L[i * N + i];
+    for (int i = 0; i < N; ++i) y[i] = b[i];
+    for (int k = N - 1; k >= 0; --k) {
+      y[k] *= L[k * N + k];
+      for (int i = P.parent[k]; i >= 0; i = P.parent[i]) y[i] -= L[k * N + i] * y[k];
     }
-    for (int i = N - 1; i >= 0; --i) {
-      R t = y[i];
-      for (int k = i + 1; k < N; ++k) t -= L[k * N + i] * x[k];
-      x[i] = t * L[i * N + i];
+    for (int k = 0; k < N; ++k) {
+      R t = y[k];
+      for (int i = P.parent[k]; i >= 0; i = P.parent[i]) t -= L[k * N + i] * x[i];
+      x[k] = t * L[k * N + k];
     }
   }
 
@@ -455,7 +483,7 @@ struct SysRigid {
     rnea<R, R>(P, q, qd, z, true, KIND == RK_QUAD, h);
     mass_chol(P, q, L);
     for (int i = 0; i < N; ++i) rhs[i] = tau[i] - h[i];
-    chol_solve(L, rhs, qdd);
+    chol_solve(P, L, rhs, qdd);
   }
 
   template <class R>
@@ -660,12 +688,12 @@ struct SysRigid {
       R t[3], rw[3];
       cross(r, pw, rw);
       for (int k = 0; k < 3; ++k) t[k] = pv[k] - rw[k];
-      mv(E, pw, pr.Epw[i]);
-      mv(E, t, pr.Ept[i]);
+      jmv(P.jtype[i], E, pw, pr.Epw[i]);
+      jmv(P.jtype[i], E, t, pr.Ept[i]);
       cross(r, paw, rw);
       for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
-      mv(E, paw, pr.Epa[i]);
-      mv(E, t, pr.Epb[i]);
+      jmv(P.jtype[i], E, paw, pr.Epa[i]);
+      jmv(P.jtype[i], E, t, pr.Epb[i]);
       const int jt = P.jtype[i];
       R sw[3] = {R(0), R(0), R(0)}, sv[3] = {R(0), R(0), R(0)};
       if (jt <= 2) sw[jt] = pr.qd[i]; else sv[jt - 3] = pr.qd[i];
@@ -734,8 +762,8 @@ struct SysRigid {
       const int pa = P.parent[i];
       if (pa >= 0) {
         R en[3], ef[3], rf[3];
-        mtv(pr.E[i], pr.fn[i], en);
-        mtv(pr.E[i], pr.ff[i], ef);
+        jmtv(jt, pr.E[i], pr.fn[i], en);
+        jmtv(jt, pr.E[i], pr.ff[i], ef);
         cross(pr.r[i], ef, rf);
         for (int k = 0; k < 3; ++k) { pr.fn[pa][k] += en[k] + rf[k]; pr.ff[pa][k] += ef[k]; }
       }
@@ -772,27 +800,27 @@ struct SysRigid {
       }
       // velocity
       R t[3], u3[3];
-      mv(E, dpw, dvw[i]);
+      jmv(jt, E, dpw, dvw[i]);
       rot_tangent(ax, rev ? sq : R(0), pr.Epw[i], dvw[i]);
       for (int k = 0; k < 3; ++k) t[k] = dpv[k];
       cross(r, dpw, u3);
       for (int k = 0; k < 3; ++k) t[k] -= u3[k];
       cross(dr, pw, u3);
       for (int k = 0; k < 3; ++k) t[k] -= u3[k];
-      mv(E, t, dvv[i]);
+      jmv(jt, E, t, dvv[i]);
       rot_tangent(ax, rev ? sq : R(0), pr.Ept[i], dvv[i]);
       R sw[3] = {R(0), R(0), R(0)}, sv[3] = {R(0), R(0), R(0)}, dsw[3] = {R(0), R(0), R(0)}, dsv[3] = {R(0), R(0), R(0)};
       if (rev) { sw[ax] = pr.qd[i]; dsw[ax] = dqd[i]; } else { sv[ax] = pr.qd[i]; dsv[ax] = dqd[i]; }
       for (int k = 0; k < 3; ++k) { dvw[i][k] += dsw[k]; dvv[i][k] += dsv[k]; }
       // acceleration (qdd fixed)
-      mv(E, dpaw, daw[i]);
+      jmv(jt, E, dpaw, daw[i]);
       rot_tangent(ax, rev ? sq : R(0), pr.Epa[i], daw[i]);
       for (int k = 0; k < 3; ++k) t[k] = dpav[k];
       cross(r, dpaw, u3);
       for (int k = 0; k < 3; ++k) t[k] -= u3[k];
       cross(dr, paw, u3);
       for (int k = 0; k < 3; ++k) t[k] -= u3[k];
-      mv(E, t, dav[i]);
+      jmv(jt, E, t, dav[i]);
       rot_tangent(ax, rev ? sq : R(0), pr.Epb[i], dav[i]);
       cross_acc(dvw[i], sw, daw[i]);
       cross_acc(pr.vw[i], dsw, daw[i]);
@@ -887,11 +915,11 @@ struct SysRigid {
           axis_cross(ax, pr.ff[i], w1);
           for (int k = 0; k < 3; ++k) yf[k] += dq[i] * w1[k];
         }
-        mtv(E, yn, den);
-        mtv(E, yf, def);
+        jmtv(jt, E, yn, den);
+        jmtv(jt, E, yf, def);
         R ef[3], dr[3] = {R(0), R(0), R(0)};
         if (!rev) dr[ax] = dq[i];
-        mtv(E, pr.ff[i], ef);
+        jmtv(jt, E, pr.ff[i], ef);
         cross_acc(dr, ef, den);
         cross_acc(pr.r[i], def, den);
         for (int k = 0; k < 3; ++k) { dfn[pa][k] += den[k]; dff[pa][k] += def[k]; }
@@ -933,7 +961,7 @@ struct SysRigid {
         R dtau[N], rhs[N], dqdd[N];
         rnea_tangent(P, pr, dq, dqd, dtau);
         for (int i = 0; i < N; ++i) rhs[i] = ((c >= n && i == A0 + (c - n)) ? R(1) : R(0)) - dtau[i];
-        chol_solve(pr.L, rhs, dqdd);
+        chol_solve(P, pr.L, rhs, dqdd);
         for (int i = 0; i < N; ++i) {
           dqd[i] = dqd[i] + h * dqdd[i];
           dq[i] = dq[i] + h * dqd[i];

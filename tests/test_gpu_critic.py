@@ -37,8 +37,10 @@ def test_critic_targets_match_the_definition(P, oracle_mod, make, prec):
             np.testing.assert_allclose(V[i, :T + 1], ref, rtol=1e-12, atol=0)
             assert np.all(V[i, T + 1:] == 0)
         if K == T_max:
-            # the whole-horizon window is the solve's final cost
-            np.testing.assert_allclose(V[:, 0], r["J"], rtol=1e-12 if prec == "fp64" else 1e-6)
+            # the whole-horizon window is the solve's final cost (in mixed mode
+            # the solver's own J comes from float32 cost evaluations: a small
+            # terminal distance |ee - target| loses digits to cancellation)
+            np.testing.assert_allclose(V[:, 0], r["J"], rtol=1e-12 if prec == "fp64" else 1e-5)
 
 
 def test_critic_targets_reject_bad_window(P):
