@@ -670,11 +670,11 @@ static int chol_guarded(int m, const double* Quu, double* L) {
 
 // Levenberg-Marquardt variant (Sec. IV-B's standard regularisation): factor
 // Q_uu + mu I under the pivot test d_j > 1e-12 (max|diag Q_uu| + mu); 0 ok,
-// -3 when mu must grow, -1 on a non-finite Q_uu
+// -3 when mu must grow (a non-finite Q_uu included: the backward pass failed)
 static int chol_shifted(int m, const double* Quu, double mu, double* L) {
   double mx = 0;
   for (int i = 0; i < m; ++i) mx = std::max(mx, std::fabs(Quu[i * m + i]));
-  if (!std::isfinite(mx)) return -1;
+  if (!std::isfinite(mx)) return -3;
   std::vector<double> R(Quu, Quu + m * m);
   for (int i = 0; i < m; ++i) R[i * m + i] += mu;
   return chol_factor(m, R.data(), 1e-12 * (mx + mu), L) ? 0 : -3;

@@ -211,7 +211,7 @@ struct Solver {
     for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(w.Quu[i * m + i]));
     w.mu = mu;
     w.flag = 3;
-    if (!isfinite(mx)) { w.flag = 2; return; }
+    if (!isfinite(mx)) return;
     if (chol(w.Quu, mu, 1e-12 * (mx + mu), w.L)) {
       w.flag = 0;
       for (int i = 0; i < m * m; ++i) w.Lf[i] = (R)w.L[i];
@@ -692,8 +692,11 @@ struct Solver {
             const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, gains + kk * GS,
                                         (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, mu_lm, timer, tlast);
             if (f == 1) flags |= ST_FLAG_REG;
-            if (f == 2) bad = true;
-            if (f == 3) need_mu = true;
+            // Levenberg-Marquardt: any failed factor (pivot test, or a
+            // non-finite Q_uu once an earlier knot's gains were skipped)
+            // asks for a larger mu; the rest of this pass is discarded
+            if (a.lm) { if (f >= 2) need_mu = true; }
+            else if (f == 2) bad = true;
           }
         }
         if (bw && bad) {
