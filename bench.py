@@ -418,6 +418,7 @@ def run_gb300(args):
     peak32 = fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0), sms)
     peak64 = fp64_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0), sms)
     others = None if args.no_extras else config_legs(P, dev, flush, peak32, peak64)
+    bic = None if args.no_extras else bic_leg(P, peak32)
     achieved = alg / (t_local / args.steps) / 1e12
     traffic = measured_traffic()
     n = ws
@@ -475,6 +476,8 @@ def run_gb300(args):
         line["serve"] = serve
     if others is not None:
         line["other_workloads"] = others
+    if bic is not None:
+        line["bic_ranking"] = bic
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
@@ -538,6 +541,36 @@ def serve_leg(P, dev):
             server.close()
             _log(f"serve {prec_name} rate {rate:g}: {len(trace)} requests in {wall:.2f} s")
         out[prec_name] = rows
+    return out
+
+
+# --------------------------------------------------------------------------
+# biased-initial-condition ranking: 10N candidates scored by the std-critic
+# MLP, top N selected (Sec. III-D), N = 8192
+# --------------------------------------------------------------------------
+def bic_leg(P, peak32):
+    from paper_2602_19699_gb300 import workload as W
+    out = {}
+    for name, sysid in (("planar3", W.PLANAR3), ("quad", W.QUAD)):
+        prob = W.make_problem(sysid, 0)
+        N = 8192
+        Cn = 10 * N
+        X = W.make_batch(prob, Cn, seed=11).x0
+        r = P.Ranker(prob.n, W.std_critic_weights(prob.n, seed=0))
+        for _ in range(3):
+            r.rank(X, N)
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            r.rank(X, N)
+            ts.append(time.perf_counter() - t0)
+        t = float(np.median(ts))
+        flops = Cn * 2.0 * (prob.n * 256 + 256 * 256 + 256)
+        out[name] = {"candidates": Cn, "selected": N, "ms": t * 1e3, "candidates_per_s": Cn / t,
+                     "mlp_tflops": flops / t / 1e12, "frac_of_fp32_peak": flops / t / 1e12 / peak32,
+                     "timing": "host wall time of torank_candidates (H2D of the candidates, scoring, selection, "
+                               "D2H of the indices)"}
+        r.close()
     return out
 
 

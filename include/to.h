@@ -389,6 +389,26 @@ int tograph_sync(to_graph g);
 int tograph_launch_count(to_graph g);
 void tograph_destroy(to_graph g);
 
+/*
+ * Biased-initial-condition ranking (Sec. III-C/D): from the second CACTO
+ * iteration on, 10N candidate initial states are scored by the std-critic
+ * network V^std (the predicted standard deviation of the critic) and the N
+ * highest start the next TO batch.  The std-critic here is an MLP
+ * n_in -> 256 -> 256 -> 1 with tanh hidden layers and a softplus output;
+ * weights (float32, row-major out x in): W1[256 x n_in] b1[256]
+ * W2[256 x 256] b2[256] W3[1 x 256] b3[1]; 1 <= n_in <= 64.
+ * torank_candidates scores the C candidates x (host, C x n_in float64) on
+ * the device in float32 and writes the indices of the N largest scores to
+ * top_idx (host, N, ascending index order; a score tied with the N-th
+ * largest is taken by the lower index; a non-finite score ranks last);
+ * scores (host, C float32) may be NULL.  Synchronises cuda_stream.
+ * Errors: TO_ERR_ARG (sizes, 1 <= N <= C), TO_ERR_CUDA.
+ */
+typedef struct to_ranker_s* to_ranker;
+int toranker_create(int n_in, const float* weights, size_t n_weights, to_ranker* out);
+int torank_candidates(to_ranker r, int C, const double* x, int N, int* top_idx, float* scores, void* cuda_stream);
+void toranker_destroy(to_ranker r);
+
 const char* tolast_error(void);
 
 #ifdef __cplusplus

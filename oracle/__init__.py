@@ -234,6 +234,33 @@ class Oracle:
         return dict(X=X, U=U, J=J, iters=iters, status=status, Vx=Vx, K=K, alpha_hist=ah, J_hist=Jh, T=T)
 
 
+def std_critic(weights, X):
+    """The std-critic MLP (n_in -> 256 tanh -> 256 tanh -> 1 softplus) in
+    float64 on rows of X (Sec. III-C's V^std)."""
+    X = np.asarray(X, dtype=np.float64)
+    w = np.asarray(weights, dtype=np.float64)
+    n_in = X.shape[1]
+    o = 0
+    W1 = w[o:o + 256 * n_in].reshape(256, n_in); o += 256 * n_in
+    b1 = w[o:o + 256]; o += 256
+    W2 = w[o:o + 256 * 256].reshape(256, 256); o += 256 * 256
+    b2 = w[o:o + 256]; o += 256
+    W3 = w[o:o + 256].reshape(1, 256); o += 256
+    b3 = w[o:o + 1]
+    h1 = np.tanh(X @ W1.T + b1)
+    h2 = np.tanh(h1 @ W2.T + b2)
+    z = (h2 @ W3.T + b3)[:, 0]
+    return np.logaddexp(0.0, z)                  # softplus
+
+
+def rank_candidates(weights, X, N):
+    """Indices (ascending) of the N candidates with the largest std-critic
+    score, ties broken by the lower index (Sec. III-D), and the scores."""
+    s = std_critic(weights, X)
+    order = np.lexsort((np.arange(s.size), -s))  # score descending, then index
+    return np.sort(order[:N]), s
+
+
 def eigclip(Q, eps):
     Q = _arr(Q)
     n = Q.shape[0]

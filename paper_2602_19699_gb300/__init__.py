@@ -86,6 +86,10 @@ def lib():
             L.toserver_stats.argtypes = [vp, vp, vp, vp, vp]
             L.toserve_replay.argtypes = [vp, i, vp, vp, vp, vp, i, vp, vp, vp, d]
             L.toget_critic_targets.argtypes = [vp, i, vp]
+            L.toranker_create.argtypes = [i, vp, C.c_size_t, C.POINTER(vp)]
+            L.torank_candidates.argtypes = [vp, i, vp, i, vp, vp, vp]
+            L.toranker_destroy.argtypes = [vp]
+            L.toranker_destroy.restype = None
             L.totune.argtypes = [vp, i, vp, vp, C.POINTER(to_solver_opts), vp, i, vp]
             L.tograph_create.argtypes = [vp, vp, vp, i, C.POINTER(to_solver_opts), i, C.POINTER(vp)]
             L.tograph_staging.argtypes = [vp, i] + [C.POINTER(vp)] * 7
@@ -106,8 +110,36 @@ def exported_symbols():
             "tosolve_batch", "tosolve_batch_device", "toget_trajectories", "toget_history",
             "toget_device_results", "tolast_launch_count", "toget_phase_cycles", "tosolve_batch_noalloc",
             "toserver_create", "toserver_destroy", "tosubmit", "topoll", "toserver_stats", "toserve_replay",
-            "toget_critic_targets", "totune", "tograph_create", "tograph_staging", "tograph_launch", "tograph_sync", "tograph_launch_count",
+            "toget_critic_targets", "toranker_create", "torank_candidates", "toranker_destroy", "totune",
+            "tograph_create", "tograph_staging", "tograph_launch", "tograph_sync", "tograph_launch_count",
             "tograph_destroy", "tolast_error"]
+
+
+class Ranker:
+    """Biased-initial-condition ranking with the std-critic MLP (toranker_*)."""
+
+    def __init__(self, n_in: int, weights):
+        self.w = np.ascontiguousarray(weights, dtype=np.float32)
+        self.handle = C.c_void_p()
+        _check(lib().toranker_create(int(n_in), _ptr(self.w), self.w.size, C.byref(self.handle)))
+        self.n_in = int(n_in)
+
+    def rank(self, x, N: int, want_scores: bool = False, stream=None):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        Cn = x.shape[0]
+        idx = np.empty(int(N), np.int32)
+        sc = np.empty(Cn, np.float32) if want_scores else None
+        _check(lib().torank_candidates(self.handle, Cn, _ptr(x), int(N), _ptr(idx), _ptr(sc) if sc is not None else None,
+                                       stream))
+        return (idx, sc) if want_scores else idx
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.toranker_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        self.close()
 
 
 class to_tune_row(C.Structure):

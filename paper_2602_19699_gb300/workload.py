@@ -271,6 +271,19 @@ def actor_weights(seed: int, sizes=ACTOR_SIZES) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
+def std_critic_weights(n_in: int, seed: int = 0) -> np.ndarray:
+    """Seeded std-critic MLP n_in -> 256 -> 256 -> 1 (same init as the actor;
+    random weights: the ranking's cost, not its meaning)."""
+    r = _rng(seed, 8)
+    parts = []
+    sizes = (n_in, 256, 256, 1)
+    for fi, fo in zip(sizes[:-1], sizes[1:]):
+        bound = 1.0 / math.sqrt(fi)
+        parts.append(r.uniform(-bound, bound, size=(fo, fi)).ravel())
+        parts.append(r.uniform(-bound, bound, size=fo))
+    return np.concatenate(parts).astype(np.float32)
+
+
 def actor_param_count(sizes=ACTOR_SIZES) -> int:
     return sum(fo * fi + fo for fi, fo in zip(sizes[:-1], sizes[1:]))
 
