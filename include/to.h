@@ -274,7 +274,8 @@ int tolast_launch_count(to_batch b);
  * boundary, so requests arriving while others are on the GPU start at once
  * and overlap with them.  Trajectories and gains stay on the device.  Every
  * device wait is bounded: a kernel with nothing to do for ~1 ms leaves and
- * the next tosubmit / topoll relaunches it.  opts applies to every request
+ * the next tosubmit / topoll relaunches it.  Each problem's kernel takes an
+ * equal share of the GPU's resident CTAs.  opts applies to every request
  * (forced_alpha, want_vx and profile_phases are ignored).
  */
 typedef struct to_server_s* to_server;

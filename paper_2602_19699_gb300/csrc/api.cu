@@ -430,7 +430,7 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   const int prec = o->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
   // a serving kernel, or a member of a multi-system graph, takes its share of
   // the resident CTAs, so the kernels of the other problems run beside it
-  const double frac = serve ? 1.0 / std::max(1, serve->grid_share) : b->grid_frac;
+  const double frac = serve ? serve->grid_frac : b->grid_frac;
   int G = 0, gpb = 0, grid = 0;
   int rc = resolve_shape(p, o, B, frac, &G, &gpb, &grid, nullptr);
   if (rc) return rc;

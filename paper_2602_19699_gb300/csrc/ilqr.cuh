@@ -57,7 +57,7 @@ struct ServeArgs {
   int* ctl;                         // device, per launch: [0] groups solving, [1] closing latch
   volatile int* closing;            // host-mapped mirror of the latch (the host then launches anew)
   int idle_polls;                   // polls (2 us apart) with no group solving before the kernel closes
-  int grid_share;                   // host side: the kernel gets 1/grid_share of the resident blocks
+  double grid_frac;                 // host side: the kernel's share of the resident CTAs
 };
 
 struct SolveArgs {

@@ -46,6 +46,7 @@ struct Lane {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool launched[2] = {false, false};
   int cur = 0;               // launch slot of the newest launch
+  double share = 1.0;        // fraction of the resident CTAs this problem's kernel takes
   int* ctl = nullptr;        // device: two control blocks of two ints
   int* closing_h = nullptr;  // host-mapped closing latches, one per slot
   int* closing_d = nullptr;
@@ -131,7 +132,7 @@ static int pump(to_server s, Lane& L) {
   sa.ctl = L.ctl + 2 * k;
   sa.closing = L.closing_d + k;
   sa.idle_polls = 500;          // about 1 ms with no group solving before the launch closes
-  sa.grid_share = (int)s->lanes.size();
+  sa.grid_frac = L.share;
   int rc = to_launch_core(L.b, L.seats, nullptr, nullptr, nullptr, nullptr, &s->opts, L.stream[k], &sa);
   if (rc) return rc;
   SV_CK(cudaEventRecord(L.ev[k], L.stream[k]));
@@ -246,6 +247,11 @@ int toserver_create(const to_problem* problems, int n_problems, const to_solver_
     for (int i = 0; i < L.seats; ++i) L.free_seats[i] = L.seats - 1 - i;
     s->bytes += L.b->bytes;
   }
+  // Each problem's kernel takes an equal share of the resident CTAs.  (Shares
+  // weighted by per-request work measured worse: a heavy problem's closing
+  // launch and its successor then hold most of the GPU between them, and the
+  // other problems' launches wait for residency.)
+  for (int pi = 0; pi < n_problems; ++pi) s->lanes[pi].share = 1.0 / n_problems;
   *out = s;
   return TO_OK;
 }

@@ -235,6 +235,34 @@ def test_invalid_horizon_rejected_on_device(P):
     assert np.all(r["status"] == P.TO_ST_NONFINITE)
 
 
+def test_empty_batch_and_knot_capacity(P, oracle_mod):
+    """An empty batch launches nothing; horizons at T_max are exact; a batch
+    whose knots exceed the workspace (checked on the device) marks every
+    instance non-finite and computes nothing."""
+    import torch
+    prob = W.pointmass(seed=7)
+    pr = P.tocreate_problem(prob.sys, prob.params, 50)
+    opts = P.to_default_opts(prec=P.TO_FP64, max_iter=4)
+    bt = P.tocreate_batch(pr, 8, 8 * 51, opts)
+    P.tosolve_batch(pr, np.zeros((0, 4)), np.zeros(0, np.int32), opts=opts, batch=bt)
+    assert P.tolast_launch_count(bt) == 0
+    # every horizon at T_max
+    b = W.make_batch(prob, 8, seed=3, T=50)
+    o = oracle_mod.Oracle.from_problem(prob)
+    ro = o.solve(b.x0, b.T, max_iter=4)
+    P.tosolve_batch(pr, b.x0, b.T, opts=opts, batch=bt, forced_alpha=ro["alpha_hist"])
+    rg = P.toget_trajectories(bt)
+    assert np.abs(rg["J"] - ro["J"]).max() <= FP64_TOL * np.abs(ro["J"]).max()
+    # 8 instances of 50 knots do not fit a workspace of 4 x 51 knot records
+    small = P.tocreate_batch(pr, 8, 4 * 51, opts)
+    x0 = torch.tensor(b.x0, dtype=torch.float64, device="cuda")
+    T = torch.full((8,), 50, dtype=torch.int32, device="cuda")
+    P.tosolve_batch_device(small, 8, x0.data_ptr(), T.data_ptr(), opts=opts)
+    torch.cuda.synchronize()
+    r = P.toget_trajectories(small, X=False, U=False)
+    assert np.all(r["status"] == P.TO_ST_NONFINITE)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_full_size_planar3_sampled(P, oracle_mod, prec):
     """The bench workload at full size (B=8192, T in [100,400]) in the default
