@@ -326,6 +326,8 @@ def run_gb300(args):
     rng = np.random.default_rng(12345)
     idx = np.sort(rng.choice(B, size=CPU_SAMPLE, replace=False))
     ro, t_cpu, cores = cpu_baseline_leg(prob, b, idx)
+    # the same oracle on one core, on the first 8 instances of the sample
+    _, t_cpu1, _ = cpu_baseline_leg(prob, b, idx[:8], threads=1)
     frac_mixed = solved_fraction(J_g["J"][idx], ro["J"])
     two_sided = float(np.mean(np.abs(J_g["J"][idx] - ro["J"]) <= COST_TOL * np.abs(ro["J"])))
     # the oracle against itself with x0 moved by 1e-15 relative: the ceiling
@@ -468,7 +470,9 @@ def run_gb300(args):
                      "algorithmic_flops_per_launch": alg},
         "cpu_baseline": {"value": len(idx) / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{len(idx)} random instances of the same workload, FP64 C++ oracle, "
-                                   f"one instance per thread"},
+                                   f"one instance per thread",
+                         "single_core": {"value": 8 / t_cpu1, "unit": UNIT, "cores": 1,
+                                         "sample": "the first 8 instances of the same sample, one thread"}},
         "clocks": clk,
     }
     line.update(extras)
