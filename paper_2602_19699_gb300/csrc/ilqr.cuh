@@ -437,7 +437,7 @@ struct Solver {
     // V_xx <- sym(Q_xx + Q_ux^T K) in place (one lane per unordered pair),
     // V_x <- Q_x + Q_ux^T k, gains to memory
     if (act)
-      for (int e = g.lane; e < NT + n + m * (n + 1); e += G) {
+      for (int e = g.lane; e < NT + n + GS; e += G) {
         if (e < NT) {
           int i, j;
           unrank_upper(e, i, j);
@@ -458,8 +458,8 @@ struct Solver {
           w.v[i] = s;
           if (vxrec) vxrec[i] = (double)s;
         } else {
-          const int f = e - NT - n;     // K then k, adjacent in W and in memory
-          grec[f] = w.K[f];
+          const int f = e - NT - n;     // K then k, adjacent in W and in memory; then the padding
+          grec[f] = f < m * (n + 1) ? w.K[f] : R(0);
         }
       }
     g.sync();
@@ -798,6 +798,9 @@ struct Solver {
               if (kLo)
 #pragma unroll
                 for (int i = 0; i < n; ++i) r[n + m + i] = xlo[i];
+              // the padding too: whole 32-byte sectors reach L2 without a read
+#pragma unroll
+              for (int i = n + m + kLo; i < RS; ++i) r[i] = R(0);
               Jc.add(Sys::cost_step2(P, xh, xlo, uh));
             }
             g.sync();
@@ -808,9 +811,13 @@ struct Solver {
             R* r = rec(traj, base, T, slot);
 #pragma unroll
             for (int i = 0; i < n; ++i) r[i] = xh[i];
+#pragma unroll
+            for (int i = 0; i < m; ++i) r[n + i] = R(0);       // no control at the terminal knot
             if (kLo)
 #pragma unroll
               for (int i = 0; i < n; ++i) r[n + m + i] = xlo[i];
+#pragma unroll
+            for (int i = n + m + kLo; i < RS; ++i) r[i] = R(0);
             Jc.add(Sys::terminal_cost(P, xh));
             Jt = Jc.value();
             if (single || Jt < J) best = single ? 0 : j;   // strict decrease, compared in float64
