@@ -30,16 +30,6 @@ struct SysDubins {
   template <class R> using ParamsT = DubinsParams<R>;
   template <class R> struct Scratch { static constexpr int elems = 1; };
 
-  template <class R>
-  TO_DEV static void step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {
-    R s, c;
-    sincos(x[2], &s, &c);
-    xn[0] = x[0] + P.dt * (x[3] * c);
-    xn[1] = x[1] + P.dt * (x[3] * s);
-    xn[2] = x[2] + P.dt * u[0];
-    xn[3] = x[3] + P.dt * x[4];
-    xn[4] = x[4] + P.dt * u[1];
-  }
 
   template <class R>
   TO_DEV static R bumps(const ParamsT<R>& P, R px, R py) {
@@ -57,12 +47,6 @@ struct SysDubins {
     return P.wu * (u[0] * u[0] + u[1] * u[1]) + bumps(P, x[0], x[1]);
   }
 
-  template <class R>
-  TO_DEV static R cost_step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {
-    const R l = running_cost(P, x, u);
-    step(P, x, u, xn);
-    return l;
-  }
   // the same step on a state carried as (hi, lo) pairs, in place
   template <class R>
   TO_DEV static R cost_step2(const ParamsT<R>& P, R* xh, R* xl, const R* u) {

@@ -179,20 +179,6 @@ struct SysPlanar3 {
     chol3_solve(L, rhs, qdd);
   }
 
-  template <class R>
-  TO_DEV static void step(const Planar3Params<R>& P, const R* x, const R* u, R* xn) {
-    Kin<R> k;
-    kinematics(P, x, k);
-    R qdd[3], L[9];
-    forward_dynamics(P, k, x + 3, u, qdd, L);
-    const R dt = P.dt;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      R v = x[3 + i] + dt * qdd[i];
-      xn[3 + i] = v;
-      xn[i] = x[i] + dt * v;
-    }
-  }
 
   // Columns of [A | B] and the clipped running-cost derivatives.  Every lane
   // evaluates the shared primal (kinematics, M's factor, qdd); lanes 0..5
@@ -242,27 +228,6 @@ struct SysPlanar3 {
   }
 
   // running cost at (x, u) and the next state, sharing one kinematics pass
-  template <class R>
-  TO_DEV static R cost_step(const Planar3Params<R>& P, const R* x, const R* u, R* xn) {
-    Kin<R> k;
-    kinematics(P, x, k);
-    R l = P.wtau * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const R inv = R(0.5) / (P.bsig * P.bsig);
-    for (int b = 0; b < P.nb; ++b) {
-      R dx = k.P[3][0] - P.bc[b][0], dy = k.P[3][1] - P.bc[b][1];
-      l += P.bamp * exp(-(dx * dx + dy * dy) * inv);
-    }
-    R qdd[3], L[9];
-    forward_dynamics(P, k, x + 3, u, qdd, L);
-    const R dt = P.dt;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      R v = x[3 + i] + dt * qdd[i];
-      xn[3 + i] = v;
-      xn[i] = x[i] + dt * v;
-    }
-    return l;
-  }
 
   // the same step on a state carried as (hi, lo) pairs, in place
   template <class R>

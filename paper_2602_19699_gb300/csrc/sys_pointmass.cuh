@@ -26,13 +26,6 @@ struct SysPointMass {
   template <class R> using ParamsT = PointMassParams<R>;
   template <class R> struct Scratch { static constexpr int elems = 1; };
 
-  template <class R>
-  TO_DEV static void step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {
-    xn[0] = x[0] + P.dt * x[2];
-    xn[1] = x[1] + P.dt * x[3];
-    xn[2] = x[2] + P.dt * u[0];
-    xn[3] = x[3] + P.dt * u[1];
-  }
 
   template <class R>
   TO_DEV static R bumps(const ParamsT<R>& P, R px, R py) {
@@ -50,12 +43,6 @@ struct SysPointMass {
     return P.wu * (u[0] * u[0] + u[1] * u[1]) + bumps(P, x[0], x[1]);
   }
 
-  template <class R>
-  TO_DEV static R cost_step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {
-    const R l = running_cost(P, x, u);
-    step(P, x, u, xn);
-    return l;
-  }
   // the same step on a state carried as (hi, lo) pairs, in place
   template <class R>
   TO_DEV static R cost_step2(const ParamsT<R>& P, R* xh, R* xl, const R* u) {

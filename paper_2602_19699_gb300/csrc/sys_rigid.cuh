@@ -486,20 +486,6 @@ struct SysRigid {
     chol_solve(P, L, rhs, qdd);
   }
 
-  template <class R>
-  TO_DEV static void step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {
-    R q[N], qd[N], tau[N], qdd[N], L[N * N];
-    for (int i = 0; i < N; ++i) { q[i] = x[i]; qd[i] = x[N + i]; tau[i] = i < A0 ? R(0) : u[i - A0]; }
-    const R h = P.dt / (R)P.n_sub;
-    for (int s = 0; s < P.n_sub; ++s) {
-      accel(P, q, qd, tau, qdd, L);
-      for (int i = 0; i < N; ++i) {
-        qd[i] = qd[i] + h * qdd[i];
-        q[i] = q[i] + h * qd[i];
-      }
-    }
-    for (int i = 0; i < N; ++i) { xn[i] = q[i]; xn[N + i] = qd[i]; }
-  }
 
   // ---- costs ----
   template <class R, class S>
@@ -523,12 +509,6 @@ struct SysRigid {
       const R dz = x[2] - P.znom, dv = x[N] - P.vxt;
       l += P.wz * dz * dz + P.wrpy * (x[3] * x[3] + x[4] * x[4] + x[5] * x[5]) + P.wvx * dv * dv;
     }
-    return l;
-  }
-  template <class R>
-  TO_DEV static R cost_step(const ParamsT<R>& P, const R* x, const R* u, R* xn) {
-    const R l = running_cost(P, x, u);
-    step(P, x, u, xn);
     return l;
   }
   // the same step on a state carried as (hi, lo) pairs, in place
