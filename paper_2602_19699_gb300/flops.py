@@ -50,6 +50,23 @@ def riccati_flops(n: int, m: int, refine: bool) -> int:
     return f
 
 
+def cholesky_fp64_flops(m: int) -> int:
+    """The float64 share of a mixed-precision backward knot: the Q_uu
+    Cholesky (m^3/3), its pivot tests and reciprocal pivots (m^2 + 2m)."""
+    return m ** 3 // 3 + m * m + 2 * m
+
+
+def mixed_fp64_fraction(sys: int, n: int, m: int, total_per_knot_iter: float) -> float:
+    """Fraction of a mixed solve's algorithmic FLOPs that run in float64."""
+    return cholesky_fp64_flops(m) / max(total_per_knot_iter, 1.0)
+
+
+def effective_peak(f32: float, f64: float, p32: float, p64: float) -> float:
+    """Peak FLOP rate of a mix of float32 and float64 work: the binding time
+    is f32 / p32 + f64 / p64 (the two pipes do not overlap in the bound)."""
+    return (f32 + f64) / (f32 / p32 + f64 / p64)
+
+
 # (primal dynamics, one directional derivative of inverse dynamics incl. the
 #  M^{-1} solve, one column of M^{-1}, clipped running-cost derivatives,
 #  running cost + step)
@@ -128,3 +145,10 @@ def solve_flops(sys: int, n: int, m: int, T: np.ndarray, iters: np.ndarray, stat
     total += float(np.sum(T * failed) * bwd)
     total += float(np.sum(T * cand) * ro)
     return total
+
+
+def solve_flops_fp64(m: int, T: np.ndarray, iters: np.ndarray, status: np.ndarray) -> float:
+    """The float64 FLOPs of a mixed solve (one Cholesky of Q_uu per backward knot)."""
+    T = np.asarray(T, dtype=np.float64)
+    failed = (np.asarray(status) & 15) == 3
+    return float(np.sum(T * (np.asarray(iters) + failed)) * cholesky_fp64_flops(m))
