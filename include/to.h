@@ -165,12 +165,17 @@ typedef struct {
   size_t hbm_budget_bytes;/* 0 = no limit; else tocreate_batch / tosolve_batch
                              refuse a workspace larger than this (TO_ERR_BUDGET) */
   int group_lanes;        /* threads per instance, one of the system's supported
-                             sizes (8/16/32 planar systems, 32 arm, 64
-                             quadruped); 0 = the totune choice, else the
-                             system's default                                 */
+                             sizes (1/8/16/32 point mass, planar arm and
+                             Dubins car, 32 arm, 64 quadruped); 0 = the totune
+                             choice, else the system's default.  1: one thread
+                             per instance with every per-knot matrix in
+                             registers; its line search tries one step size
+                             at a time (the smallest j first), the others
+                             min(group_lanes, 16) at once                     */
   int groups_per_block;   /* instances resident per CTA (group_lanes x
                              groups_per_block <= 256, a multiple of 32);
-                             0 = the totune choice, else the default          */
+                             0 = the totune choice, else the default (64
+                             threads per CTA for a non-default group size)   */
   int profile_phases;     /* 1: accumulate per-phase clock64 cycles (tracing;
                              see toget_phase_cycles); 0 = off                 */
   int reg;                /* TO_REG_CLIP (default): eigenvalue clipping of the

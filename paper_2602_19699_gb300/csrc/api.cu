@@ -401,7 +401,10 @@ static int resolve_shape(to_problem p, const to_solver_opts* o, int B, double fr
     gpb = p->tuned_gpb[prec];
   }
   if (!G) G = ops->default_G;
-  if (!gpb) gpb = ops->default_gpb[prec];
+  if (!gpb) {
+    gpb = ops->default_gpb[prec];
+    if (G <= 32 && (G * gpb) % 32 != 0) gpb = 64 / G;   // a group size other than the default: 64-thread CTAs
+  }
   bool okG = false;
   for (int i = 0; i < ops->n_groups; ++i) okG |= ops->groups[i] == G;
   if (!okG) return fail(TO_ERR_ARG, "opts: group_lanes not supported by this system");

@@ -12,10 +12,11 @@ enum { PREC_FP64 = 0, PREC_MIXED = 1 };
 
 // A group of G threads owns one instance.  G <= 32: 32/G groups share a warp
 // and every warp runs warp-uniform control flow (work is predicated per group),
-// so a group barrier is a warp barrier.  G > 32: one group per CTA.
+// so a group barrier is a warp barrier.  G > 32: one group per CTA.  G = 1:
+// one thread per instance (32 instances per warp).
 template <int G>
 struct Group {
-  static_assert(G == 4 || G == 8 || G == 16 || G == 32 || G == 64 || G == 128 || G == 256, "group size");
+  static_assert(G == 1 || G == 4 || G == 8 || G == 16 || G == 32 || G == 64 || G == 128 || G == 256, "group size");
   static constexpr bool kSubWarp = G <= 32;
   int lane;    // 0..G-1
   int index;   // group index within the CTA
@@ -98,6 +99,36 @@ TO_DEV void semi_implicit2(R* qh, R* ql, R* vh, R* vl, const R* a, R h) {
 // clip of a zero eigenvalue, max(0, eps): the value a Hessian's entries
 // outside a cost's support take (0 when clipping is off, eps < 0)
 template <class R> TO_DEV R clip0(R eps) { return eps > R(0) ? eps : R(0); }
+
+// max(a, |x|) ignoring a NaN x, in the operands' own precision
+TO_DEV float max_abs(float a, float x) { return fmaxf(a, fabsf(x)); }
+TO_DEV double max_abs(double a, double x) { return fmax(a, fabs(x)); }
+
+// 16-byte vector moves of a record (the record and its address 16-byte aligned)
+TO_DEV void ld16(const float* p, float* d) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+}
+TO_DEV void ld16(const double* p, double* d) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  d[0] = t.x; d[1] = t.y;
+}
+TO_DEV void st16(float* p, const float* s) { *reinterpret_cast<float4*>(p) = make_float4(s[0], s[1], s[2], s[3]); }
+TO_DEV void st16(double* p, const double* s) { *reinterpret_cast<double2*>(p) = make_double2(s[0], s[1]); }
+template <int NE, class R>
+TO_DEV void ld_vec(const R* p, R* d) {
+  constexpr int V = 16 / (int)sizeof(R);
+  static_assert(NE % V == 0, "whole 16-byte vectors");
+#pragma unroll
+  for (int i = 0; i < NE; i += V) ld16(p + i, d + i);
+}
+template <int NE, class R>
+TO_DEV void st_vec(R* p, const R* s) {
+  constexpr int V = 16 / (int)sizeof(R);
+  static_assert(NE % V == 0, "whole 16-byte vectors");
+#pragma unroll
+  for (int i = 0; i < NE; i += V) st16(p + i, s + i);
+}
 
 template <class R> TO_DEV R rsqrt_(R x);
 template <> TO_DEV float rsqrt_(float x) { return rsqrtf(x); }

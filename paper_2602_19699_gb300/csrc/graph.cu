@@ -66,12 +66,13 @@ int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* 
   const int prec = opts->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
   int best_G = 0, best_gpb = 0, n = 0;
   double best_ms = INFINITY;
-  const int gpbs[] = {1, 2, 4, 8, 16, 32};
+  const int cta_threads[] = {32, 64, 128, 256};
   for (int gi = 0; gi < ops->n_groups; ++gi) {
     const int G = ops->groups[gi];
-    for (int gpb : gpbs) {
+    for (int threads : cta_threads) {
+      if (G > 32 && threads != 32) continue;            // one group per CTA: a single shape
+      const int gpb = G > 32 ? 1 : threads / G;
       if (G * gpb > kMaxCtaThreads) continue;
-      if (G <= 32 ? (G * gpb) % 32 != 0 : gpb != 1) continue;
       to_solver_opts o = base;
       o.group_lanes = G;
       o.groups_per_block = gpb;

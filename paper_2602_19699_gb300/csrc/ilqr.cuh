@@ -26,6 +26,8 @@
 // solve are float64; the cost is accumulated as a compensated float32 pair
 // (about 48 significant bits) and compared in float64.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace to {
@@ -161,6 +163,14 @@ struct Work {
   int wslot;             // slot of the accepted line-search candidate
 };
 
+// per-lane workspace of single-lane groups: every matrix lives in registers
+struct WorkLane {
+  double red;
+  int flag;
+  int sel;
+  int wslot;
+};
+
 enum { M_IDLE = 0, M_NEW, M_RUN, M_FINAL, M_DRAINED };
 
 // Levenberg-Marquardt variant: mu starts at kMu0, is multiplied by kMuFactor
@@ -181,7 +191,9 @@ struct Solver {
   static constexpr int NS = LW + 1;                        // trajectory slots per knot
   static constexpr int kRounds = (kMaxAlpha + LW - 1) / LW; // most line-search rounds
   typedef typename Sys::template ParamsT<R> Params;
-  typedef Work<Sys, R> W;
+  static constexpr bool kLane = (G == 1);                  // one thread per instance, matrices in registers
+  typedef std::conditional_t<kLane, WorkLane, Work<Sys, R>> W;
+  static_assert(!(kLane && Sys::kActor), "the actor warm start needs a lane group");
 
   // ------------------------------------------------------------------------
   // Cholesky of Q_uu in float64 with the pivot test  d_j > 1e-12 max|diag|;
@@ -189,52 +201,68 @@ struct Solver {
   // Levenberg-Marquardt term, used only as this guard).  One thread; the
   // reciprocal pivots come from rsqrt, so there is no float64 division.
   // ------------------------------------------------------------------------
+  template <bool kShift>
   TO_DEV static bool chol(const double* A, double shift, double delta, double* L) {
+#pragma unroll
     for (int j = 0; j < m; ++j) {
-      double s = A[j * m + j] + shift;
+      double s = A[j * m + j];
+      if (kShift) s += shift;
       for (int k = 0; k < j; ++k) s -= L[j * m + k] * L[j * m + k];
       if (!(s > delta)) return false;
       const double r = rsqrt(s);
       L[j * m + j] = r;                      // stores 1 / L_jj
+#pragma unroll
       for (int i = j + 1; i < m; ++i) {
         double t = A[i * m + j];
+#pragma unroll
         for (int k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
         L[i * m + j] = t * r;
       }
     }
     return true;
   }
-  // Levenberg-Marquardt variant (Sec. IV-B's standard regularisation): the
-  // factor of Q_uu + mu I with the pivot test; flag 3 asks for a larger mu
-  TO_DEV static void chol_lm(W& w, double mu) {
-    double mx = 0;
-    for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(w.Quu[i * m + i]));
-    w.mu = mu;
-    w.flag = 3;
-    if (!isfinite(mx)) return;
-    if (chol(w.Quu, mu, 1e-12 * (mx + mu), w.L)) {
-      w.flag = 0;
-      for (int i = 0; i < m * m; ++i) w.Lf[i] = (R)w.L[i];
-    }
-  }
-  TO_DEV static void chol_guarded(W& w) {
-    double mx = 0;
-    for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(w.Quu[i * m + i]));
-    w.mu = 0;
-    w.flag = 2;
-    if (!(mx > 0) || !isfinite(mx)) return;
-    const double delta = 1e-12 * mx;
-    if (chol(w.Quu, 0.0, delta, w.L)) {
-      w.flag = 0;
+  // The float64 factor of Q_uu with the pivot test.  lm = 0: the guard
+  // above (flag 0 plain, 1 regularised with mu, 2 failed).  lm = 1: the
+  // Levenberg-Marquardt variant (Sec. IV-B's standard regularisation), the
+  // factor of Q_uu + mu I with the instance's mu (flag 0, or 3: a larger mu
+  // is needed).  Q is Q_uu in float64 and Qr the same entries in R (the
+  // largest diagonal magnitude is exact in either).  On success the factor's
+  // lower triangle is also rounded to R in Lf.
+  TO_DEV static int factor(const double* Q, const R* Qr, bool lm, double mu_lm, double* L, R* Lf, double& mu) {
+    R mxr = R(0);
+#pragma unroll
+    for (int i = 0; i < m; ++i) mxr = max_abs(mxr, Qr[i * m + i]);
+    const double mx = (double)mxr;
+    int flag;
+    if (lm) {
+      mu = mu_lm;
+      flag = 3;
+      if (isfinite(mx) && chol<true>(Q, mu, 1e-12 * (mx + mu), L)) flag = 0;
     } else {
-      double mu = 1e-6 * mx;
-      for (int t = 0; t < 40; ++t) {
-        if (chol(w.Quu, mu, delta, w.L)) { w.flag = 1; w.mu = mu; break; }
-        mu *= 10.0;
+      mu = 0;
+      flag = 2;
+      if (mx > 0 && isfinite(mx)) {
+        const double delta = 1e-12 * mx;
+        if (chol<false>(Q, 0.0, delta, L)) {
+          flag = 0;
+        } else {
+          double mt = 1e-6 * mx;
+          for (int t = 0; t < 40; ++t) {
+            if (chol<true>(Q, mt, delta, L)) { flag = 1; mu = mt; break; }
+            mt *= 10.0;
+          }
+        }
       }
     }
-    if (w.flag != 2)
-      for (int i = 0; i < m * m; ++i) w.Lf[i] = (R)w.L[i];
+    if (flag < 2)
+#pragma unroll
+      for (int i = 0; i < m; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) Lf[i * m + j] = (R)L[i * m + j];
+    return flag;
+  }
+  TO_DEV static void chol_group(W& w, bool lm, double mu_lm) {
+    w.flag = factor(w.Quu, w.Quf, lm, mu_lm, w.L, w.Lf, w.mu);
   }
 
   // x = (L L^T)^{-1} b with L's diagonal stored as reciprocals
@@ -258,13 +286,14 @@ struct Solver {
   }
 
   // gain column c (c < n: K[:, c] from -Q_ux[:, c]; c == n: k from -Q_u)
-  TO_DEV static void gain_column(W& w, int c, int refine) {
+  TO_DEV static void gain_col(int c, int refine, const R* Qux, const R* Qu, const double* Quu, const R* Quf,
+                              const double* L, const R* Lf, double mu, R* K, R* kf) {
     R out[m];
     if (sizeof(R) == sizeof(double)) {
       double b[m], x[m];
 #pragma unroll
-      for (int i = 0; i < m; ++i) b[i] = -(double)(c < n ? w.Qux[i * n + c] : w.Qu[i]);
-      chol_apply<double, double>(w.L, b, x);
+      for (int i = 0; i < m; ++i) b[i] = -(double)(c < n ? Qux[i * n + c] : Qu[i]);
+      chol_apply<double, double>(L, b, x);
 #pragma unroll
       for (int i = 0; i < m; ++i) out[i] = (R)x[i];
     } else {
@@ -276,20 +305,20 @@ struct Solver {
       // refine = 2 forms it in native float64.
       float b[m], x[m];
 #pragma unroll
-      for (int i = 0; i < m; ++i) b[i] = -(float)(c < n ? w.Qux[i * n + c] : w.Qu[i]);
-      chol_apply<float, R>(w.Lf, b, x);
+      for (int i = 0; i < m; ++i) b[i] = -(float)(c < n ? Qux[i * n + c] : Qu[i]);
+      chol_apply<float, R>(Lf, b, x);
       if (refine) {
         float r[m], d[m];
         if (refine == 2) {
 #pragma unroll
           for (int i = 0; i < m; ++i) {
-            double t = (double)b[i] - w.mu * (double)x[i];
+            double t = (double)b[i] - mu * (double)x[i];
 #pragma unroll
-            for (int k = 0; k < m; ++k) t = fma(-w.Quu[i * m + k], (double)x[k], t);
+            for (int k = 0; k < m; ++k) t = fma(-Quu[i * m + k], (double)x[k], t);
             r[i] = (float)t;
           }
         } else {
-          const float muf = (float)w.mu;
+          const float muf = (float)mu;
 #pragma unroll
           for (int i = 0; i < m; ++i) {
             Acc<float> t;
@@ -301,7 +330,7 @@ struct Solver {
             }
 #pragma unroll
             for (int k = 0; k < m; ++k) {
-              const float q = (float)w.Quf[i * m + k];
+              const float q = (float)Quf[i * m + k];
               const float p = q * x[k];
               t.add(-p);
               t.add(-fmaf(q, x[k], -p));
@@ -309,7 +338,7 @@ struct Solver {
             r[i] = t.hi + t.lo;
           }
         }
-        chol_apply<float, R>(w.Lf, r, d);
+        chol_apply<float, R>(Lf, r, d);
 #pragma unroll
         for (int i = 0; i < m; ++i) x[i] += d[i];
       }
@@ -318,11 +347,15 @@ struct Solver {
     }
     if (c < n) {
 #pragma unroll
-      for (int i = 0; i < m; ++i) w.K[i * n + c] = out[i];
+      for (int i = 0; i < m; ++i) K[i * n + c] = out[i];
     } else {
 #pragma unroll
-      for (int i = 0; i < m; ++i) w.kf[i] = out[i];
+      for (int i = 0; i < m; ++i) kf[i] = out[i];
     }
+  }
+
+  TO_DEV static void gain_column(W& w, int c, int refine) {
+    gain_col(c, refine, w.Qux, w.Qu, w.Quu, w.Quf, w.L, w.Lf, w.mu, w.K, w.kf);
   }
 
   // e-th entry (row-major) of the upper triangle of an n x n matrix -> (i, j)
@@ -425,8 +458,7 @@ struct Solver {
     g.sync();
     TO_TICK(2);
     if (act && g.lane == 0) {
-      if (a.lm) chol_lm(w, mu_lm);
-      else chol_guarded(w);
+      chol_group(w, a.lm, mu_lm);
     }
     g.sync();
     const int flag = act ? w.flag : 0;
@@ -467,6 +499,145 @@ struct Solver {
     return flag;
   }
 
+  // ------------------------------------------------------------------------
+  // The backward pass of a single-lane group (G == 1).  One thread owns the
+  // instance and every per-knot matrix stays in registers (each loop over the
+  // compile-time dimensions unrolls), so there is no barrier and no
+  // shared-memory traffic, and each float64 instruction of the Q_uu Cholesky
+  // serves the 32 instances of the warp.  Same steps and summation order as
+  // backward_knot; the pass stops at the first knot whose factor fails (the
+  // instance is then released, or redone with a larger mu).
+  // ------------------------------------------------------------------------
+  TO_DEV static void backward_lane(const Params& P, const SolveArgs& a, R* traj, R* gains, long long base, int T,
+                                   int cur, double mu_lm, int& flags, bool& bad, bool& need_mu, bool timer,
+                                   long long& tlast) {
+    const R eps = (R)a.eps;
+    double* vx = (a.vx && a.want_vx) ? a.vx : nullptr;
+    R V[n * n], v[n], nx[RS];
+    ld_vec<RS>(rec(traj, base, T, cur), nx);
+    Sys::terminal_derivs(P, nx, eps, V, v);
+    if (vx)
+#pragma unroll
+      for (int i = 0; i < n; ++i) vx[(base + T) * n + i] = (double)v[i];
+    ld_vec<RS>(rec(traj, base, T - 1, cur), nx);
+    for (int k = T - 1; k >= 0; --k) {
+      R x[n], u[m];
+#pragma unroll
+      for (int i = 0; i < n; ++i) x[i] = nx[i];
+#pragma unroll
+      for (int i = 0; i < m; ++i) u[i] = nx[n + i];
+      if (k >= 1) ld_vec<RS>(rec(traj, base, k - 1, cur), nx);
+      R A[n * n], Bm[n * m], lxx[n * n], lx[n], luu[m * m], lu[m];
+      Sys::derivs_lane(P, x, u, eps, A, Bm, lxx, lx, luu, lu);
+      TO_TICK(1);
+      // Q_xx (upper triangle, mirrored) and Q_ux from the columns of V A,
+      // Q_uu from the columns of V B
+      R Qxx[n * n], Qux[m * n], Quf[m * m], Qx[n], Qu[m];
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        R c[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          R t = 0;
+#pragma unroll
+          for (int r = 0; r < n; ++r) t += V[i * n + r] * A[r * n + j];
+          c[i] = t;
+        }
+#pragma unroll
+        for (int i = 0; i <= j; ++i) {
+          R t = lxx[i * n + j];
+#pragma unroll
+          for (int r = 0; r < n; ++r) t += A[r * n + i] * c[r];
+          Qxx[i * n + j] = t;
+          Qxx[j * n + i] = t;
+        }
+#pragma unroll
+        for (int i = 0; i < m; ++i) {
+          R t = 0;
+#pragma unroll
+          for (int r = 0; r < n; ++r) t += Bm[r * m + i] * c[r];
+          Qux[i * n + j] = t;                     // Q_ux (l_ux = 0)
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < m; ++j) {
+        R c[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          R t = 0;
+#pragma unroll
+          for (int r = 0; r < n; ++r) t += V[i * n + r] * Bm[r * m + j];
+          c[i] = t;
+        }
+#pragma unroll
+        for (int i = 0; i < m; ++i) {
+          R t = luu[i * m + j];
+#pragma unroll
+          for (int r = 0; r < n; ++r) t += Bm[r * m + i] * c[r];
+          Quf[i * m + j] = t;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        R t = lx[i];
+#pragma unroll
+        for (int r = 0; r < n; ++r) t += A[r * n + i] * v[r];
+        Qx[i] = t;
+      }
+#pragma unroll
+      for (int i = 0; i < m; ++i) {
+        R t = lu[i];
+#pragma unroll
+        for (int r = 0; r < n; ++r) t += Bm[r * m + i] * v[r];
+        Qu[i] = t;
+      }
+      TO_TICK(2);
+      double Q[m * m], L[m * m], mu;
+      R Lf[m * m];
+#pragma unroll
+      for (int i = 0; i < m * m; ++i) Q[i] = (double)Quf[i];
+      const int f = factor(Q, Quf, a.lm, mu_lm, L, Lf, mu);
+      if (f == 1) flags |= ST_FLAG_REG;
+      if (a.lm) {
+        if (f >= 2) { need_mu = true; break; }
+      } else if (f == 2) {
+        bad = true;
+        break;
+      }
+      R g[GS];                                    // gain record: K, k, padding
+#pragma unroll
+      for (int c = 0; c <= n; ++c) gain_col(c, a.refine, Qux, Qu, Q, Quf, L, Lf, mu, g, g + m * n);
+#pragma unroll
+      for (int i = m * (n + 1); i < GS; ++i) g[i] = R(0);
+      TO_TICK(3);
+      // V_xx <- sym(Q_xx + Q_ux^T K), V_x <- Q_x + Q_ux^T k, gains to memory
+#pragma unroll
+      for (int i = 0; i < n; ++i)
+#pragma unroll
+        for (int j = i; j < n; ++j) {
+          R sij = Qxx[i * n + j], sji = Qxx[j * n + i];
+#pragma unroll
+          for (int r = 0; r < m; ++r) {
+            sij += Qux[r * n + i] * g[r * n + j];
+            sji += Qux[r * n + j] * g[r * n + i];
+          }
+          const R t = R(0.5) * (sij + sji);
+          V[i * n + j] = t;
+          V[j * n + i] = t;
+        }
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        R t = Qx[i];
+#pragma unroll
+        for (int r = 0; r < m; ++r) t += Qux[r * n + i] * g[m * n + r];
+        v[i] = t;
+        if (vx) vx[(base + k) * n + i] = (double)t;
+      }
+      st_vec<GS>(gains + (base + k) * GS, g);
+      TO_TICK(4);
+    }
+  }
+
   // forward record (x_k, u_k, K_k, k_k, x_lo) element e of the lane's prefetch slot
   TO_DEV static R load_fwd(const R* trec, const R* grec, int e) {
     constexpr int NG = m * (n + 1);
@@ -501,6 +672,34 @@ struct Solver {
       for (int j = 0; j < n; ++j) s += w.K[i * n + j] * dx[j];
       uh[i] = s;
     }
+  }
+
+  // the same from a record and gain record held in registers (single lane)
+  TO_DEV static void policy_regs(const R* cr, const R* cg, R alpha, const R* xh, const R* xlo, R* uh) {
+    R dx[n];
+#pragma unroll
+    for (int j = 0; j < n; ++j) dx[j] = kLo ? (xh[j] - cr[j]) + (xlo[j] - cr[n + m + j]) : xh[j] - cr[j];
+#pragma unroll
+    for (int i = 0; i < m; ++i) {
+      R s = cr[n + i] + alpha * cg[m * n + i];
+#pragma unroll
+      for (int j = 0; j < n; ++j) s += cg[i * n + j] * dx[j];
+      uh[i] = s;
+    }
+  }
+
+  // knot record [x | u | x_lo | 0...] written with 16-byte stores
+  TO_DEV static void put_record(R* r, const R* xh, const R* uh, const R* xlo) {
+    R o[RS];
+#pragma unroll
+    for (int i = 0; i < n; ++i) o[i] = xh[i];
+#pragma unroll
+    for (int i = 0; i < m; ++i) o[n + i] = uh[i];
+#pragma unroll
+    for (int i = 0; i < kLo; ++i) o[n + m + i] = xlo[i];
+#pragma unroll
+    for (int i = n + m + kLo; i < RS; ++i) o[i] = R(0);
+    st_vec<RS>(r, o);
   }
 
   // actor policy u = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3 (Sec. II: the
@@ -661,8 +860,11 @@ struct Solver {
       // ---- phase A: backward pass along slot cur
       {
         const bool bw = (mode == M_RUN || mode == M_FINAL) && !release;
-        const int kmax = g.uniform_max(bw ? T : 0, &w.sel);
         bool bad = false, need_mu = false;
+        if constexpr (kLane) {
+          if (bw) backward_lane(P, a, traj, gains, base, T, cur, mu_lm, flags, bad, need_mu, timer, tlast);
+        } else {
+        const int kmax = g.uniform_max(bw ? T : 0, &w.sel);
         if (kmax > 0) {
           R pb[PB];
           if (bw) {
@@ -698,6 +900,7 @@ struct Solver {
             if (a.lm) { if (f >= 2) need_mu = true; }
             else if (f == 2) bad = true;
           }
+        }
         }
         if (bw && bad) {
           status = ST_NONFINITE;
@@ -739,7 +942,8 @@ struct Solver {
           const bool nominal = need && mode != M_NEW;   // needs the current iterate and gains
           R xh[n], xlo[n];   // the candidate's state as (hi, lo) pairs (lo = 0 in float64)
           Acc<R> Jc;
-          R pf[PF];
+          R pf[kLane ? 1 : PF];
+          R pr[kLane ? RS : 1], pg[kLane ? GS : 1];   // single lane: next knot's record and gains
           if (mine) {
             if (mode == M_NEW) {
 #pragma unroll
@@ -757,13 +961,34 @@ struct Solver {
               }
             }
           }
-          if (nominal) prefetch_fwd(g, pf, rec(traj, base, 0, cur), gains + base * GS);
+          if (nominal) {
+            if constexpr (kLane) {
+              ld_vec<RS>(rec(traj, base, 0, cur), pr);
+              ld_vec<GS>(gains + base * GS, pg);
+            } else {
+              prefetch_fwd(g, pf, rec(traj, base, 0, cur), gains + base * GS);
+            }
+          }
           const int kr = g.uniform_max(need ? T : 0, &w.sel);
           for (int k = 0; k < kr; ++k) {
             const bool act = need && k < T;
-            if (act && nominal) store_fwd(g, w, pf);
-            g.sync();
-            if (act && nominal && k + 1 < T) prefetch_fwd(g, pf, rec(traj, base, k + 1, cur), gains + (base + k + 1) * GS);
+            R cr[kLane ? RS : 1], cg[kLane ? GS : 1];
+            if constexpr (kLane) {
+              if (act && nominal) {
+#pragma unroll
+                for (int i = 0; i < RS; ++i) cr[i] = pr[i];
+#pragma unroll
+                for (int i = 0; i < GS; ++i) cg[i] = pg[i];
+                if (k + 1 < T) {
+                  ld_vec<RS>(rec(traj, base, k + 1, cur), pr);
+                  ld_vec<GS>(gains + (base + k + 1) * GS, pg);
+                }
+              }
+            } else {
+              if (act && nominal) store_fwd(g, w, pf);
+              g.sync();
+              if (act && nominal && k + 1 < T) prefetch_fwd(g, pf, rec(traj, base, k + 1, cur), gains + (base + k + 1) * GS);
+            }
             if constexpr (Sys::kActor) {
               // warm start from the actor policy u_k = pi(x_k): the group
               // evaluates the MLP, lane 0 then steps the dynamics
@@ -779,45 +1004,32 @@ struct Solver {
             if (act && mine) {
               R uh[m];
               if (mode == M_NEW) {
-                if (Sys::kActor && actor_rnd) {
+                bool from_actor = false;
+                if constexpr (Sys::kActor) {
+                  from_actor = actor_rnd;
+                  if (from_actor)
 #pragma unroll
-                  for (int i = 0; i < m; ++i) uh[i] = w.uk[i];
-                } else {
+                    for (int i = 0; i < m; ++i) uh[i] = w.uk[i];
+                }
+                if (!from_actor)
 #pragma unroll
                   for (int i = 0; i < m; ++i)
                     uh[i] = a.U_init ? (R)a.U_init[((size_t)inst * a.T_max + k) * m + i] : R(0);
-                }
               } else {
-                policy(w, alpha, xh, xlo, uh);
+                if constexpr (kLane) policy_regs(cr, cg, alpha, xh, xlo, uh);
+                else policy(w, alpha, xh, xlo, uh);
               }
-              R* r = rec(traj, base, k, slot);
-#pragma unroll
-              for (int i = 0; i < n; ++i) r[i] = xh[i];
-#pragma unroll
-              for (int i = 0; i < m; ++i) r[n + i] = uh[i];
-              if (kLo)
-#pragma unroll
-                for (int i = 0; i < n; ++i) r[n + m + i] = xlo[i];
               // the padding too: whole 32-byte sectors reach L2 without a read
-#pragma unroll
-              for (int i = n + m + kLo; i < RS; ++i) r[i] = R(0);
+              put_record(rec(traj, base, k, slot), xh, uh, xlo);
               Jc.add(Sys::cost_step2(P, xh, xlo, uh));
             }
-            g.sync();
+            if constexpr (!kLane) g.sync();
           }
           double Jt = 0;
           int best = 0x7fffffff;
           if (mine) {
-            R* r = rec(traj, base, T, slot);
-#pragma unroll
-            for (int i = 0; i < n; ++i) r[i] = xh[i];
-#pragma unroll
-            for (int i = 0; i < m; ++i) r[n + i] = R(0);       // no control at the terminal knot
-            if (kLo)
-#pragma unroll
-              for (int i = 0; i < n; ++i) r[n + m + i] = xlo[i];
-#pragma unroll
-            for (int i = n + m + kLo; i < RS; ++i) r[i] = R(0);
+            const R u0[m] = {};                                 // no control at the terminal knot
+            put_record(rec(traj, base, T, slot), xh, u0, xlo);
             Jc.add(Sys::terminal_cost(P, xh));
             Jt = Jc.value();
             if (single || Jt < J) best = single ? 0 : j;   // strict decrease, compared in float64

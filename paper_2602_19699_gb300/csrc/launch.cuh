@@ -47,15 +47,16 @@ __global__ void __launch_bounds__(kMaxCtaThreads, 1) ilqr_kernel(SolveArgs a) {
   Solver<Sys, R, G>::run(a, smem_raw);
 }
 
-template <class Sys, class R>
+template <class Sys, class R, int G>
 inline size_t solver_smem(int gpb) {
-  return ((sizeof(typename Sys::template ParamsT<R>) + 15) / 16) * 16 + (size_t)gpb * sizeof(Work<Sys, R>);
+  return ((sizeof(typename Sys::template ParamsT<R>) + 15) / 16) * 16 +
+         (size_t)gpb * sizeof(typename Solver<Sys, R, G>::W);
 }
 
 template <class Sys, class R, int G>
 inline cudaError_t launch_one(int gpb, int grid, cudaStream_t s, const SolveArgs& a) {
   const int threads = G * gpb;
-  const size_t smem = solver_smem<Sys, R>(gpb);
+  const size_t smem = solver_smem<Sys, R, G>(gpb);
   auto k = ilqr_kernel<Sys, R, G>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -65,7 +66,7 @@ inline cudaError_t launch_one(int gpb, int grid, cudaStream_t s, const SolveArgs
 
 template <class Sys, class R, int G>
 inline cudaError_t occupancy_one(int gpb, size_t* smem, int* bps) {
-  *smem = solver_smem<Sys, R>(gpb);
+  *smem = solver_smem<Sys, R, G>(gpb);
   auto k = ilqr_kernel<Sys, R, G>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
   if (e != cudaSuccess) return e;

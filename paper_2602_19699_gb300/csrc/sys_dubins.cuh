@@ -123,6 +123,28 @@ struct SysDubins {
     if (g.lane == G - 1) running_derivs(P, x, u, eps, lxx, lx, luu, lu);
   }
 
+  // the same on one lane (single-lane groups)
+  template <class R>
+  TO_DEV static void derivs_lane(const ParamsT<R>& P, const R* x, const R* u, R eps, R* A, R* B, R* lxx, R* lx,
+                                 R* luu, R* lu) {
+    R s, c;
+    sincos(x[2], &s, &c);
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+      for (int j = 0; j < n; ++j) A[i * n + j] = (i == j) ? R(1) : R(0);
+    A[0 * n + 2] = -P.dt * x[3] * s;
+    A[0 * n + 3] = P.dt * c;
+    A[1 * n + 2] = P.dt * x[3] * c;
+    A[1 * n + 3] = P.dt * s;
+    A[3 * n + 4] = P.dt;
+#pragma unroll
+    for (int i = 0; i < n * m; ++i) B[i] = R(0);
+    B[2 * m + 0] = P.dt;
+    B[4 * m + 1] = P.dt;
+    running_derivs(P, x, u, eps, lxx, lx, luu, lu);
+  }
+
   template <class R>
   TO_DEV static void terminal_derivs(const ParamsT<R>& P, const R* x, R eps, R* lxx, R* lx) {
     const R a = R(2) * P.wpT, b = R(2) * P.wvT, c = R(2) * P.waT;

@@ -227,6 +227,45 @@ struct SysPlanar3 {
     if (lane == cost_lane) running_derivs_k(P, k, u, eps, lxx, lx, luu, lu);
   }
 
+  // the same on one lane (single-lane groups): one primal, the six tangent
+  // passes, the three columns of M^{-1} and the cost terms in turn
+  template <class R>
+  TO_DEV static void derivs_lane(const Planar3Params<R>& P, const R* x, const R* u, R eps, R* A, R* B, R* lxx,
+                                 R* lx, R* luu, R* lu) {
+    const R dt = P.dt;
+    Kin<R> k;
+    kinematics(P, x, k);
+    R qdd[3], L[9], d[3];
+    forward_dynamics(P, k, x + 3, u, qdd, L);
+#pragma unroll
+    for (int c = 0; c < n; ++c) {
+      R dq[3] = {0, 0, 0}, dqd[3] = {0, 0, 0}, tau[3], dtau[3];
+      if (c < 3) dq[c] = 1; else dqd[c - 3] = 1;
+      rnea<R, true>(P, k, x + 3, qdd, tau, dq, dqd, dtau);
+      chol3_solve(L, dtau, d);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const R eq = (c == i) ? R(1) : R(0);
+        const R ev = (c == 3 + i) ? R(1) : R(0);
+        const R dv = ev - dt * d[i];
+        A[(3 + i) * n + c] = dv;
+        A[i * n + c] = eq + dt * dv;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < m; ++c) {
+      R e[3] = {0, 0, 0};
+      e[c] = 1;
+      chol3_solve(L, e, d);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        B[(3 + i) * m + c] = dt * d[i];
+        B[i * m + c] = dt * dt * d[i];
+      }
+    }
+    running_derivs_k(P, k, u, eps, lxx, lx, luu, lu);
+  }
+
   // running cost at (x, u) and the next state, sharing one kinematics pass
 
   // the same step on a state carried as (hi, lo) pairs, in place

@@ -111,6 +111,21 @@ struct SysPointMass {
     if (g.lane == G - 1) running_derivs(P, x, u, eps, lxx, lx, luu, lu);
   }
 
+  // the same on one lane (single-lane groups)
+  template <class R>
+  TO_DEV static void derivs_lane(const ParamsT<R>& P, const R* x, const R* u, R eps, R* A, R* B, R* lxx, R* lx,
+                                 R* luu, R* lu) {
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+      for (int j = 0; j < n; ++j) A[i * n + j] = (i == j) ? R(1) : ((j == i + 2) ? P.dt : R(0));
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+      for (int j = 0; j < m; ++j) B[i * m + j] = (i == j + 2) ? P.dt : R(0);
+    running_derivs(P, x, u, eps, lxx, lx, luu, lu);
+  }
+
   template <class R>
   TO_DEV static void terminal_derivs(const ParamsT<R>& P, const R* x, R eps, R* lxx, R* lx) {
     const R a = R(2) * P.wpT, b = R(2) * P.wvT;
