@@ -117,11 +117,16 @@ enum {
  *     [C+12] end-effector body [C+13..15] end-effector point in that body
  *     l_k = w_tau |u|^2 + sum_b amp exp(-|ee(q) - c_b|^2 / (2 sigma^2))
  *     l_T = w_ee |ee(q) - target|^2 + w_vT |qd|^2
- *   ARM7:
+ *   ARM7 (the device model is compiled for this tree: a chain, body i the
+ *     child of body i-1, joints Rz Ry Rz Ry Rz Ry Rz; other trees are
+ *     rejected with TO_ERR_ARG):
  *     [C] w_tau [C+1] w_v [C+2..4] target [C+5] w_ee [C+6] w_vT
- *     [C+7] end-effector body [C+8..10] end-effector point
+ *     [C+7] end-effector body (6) [C+8..10] end-effector point
  *     l_k = w_tau |u|^2 + w_v |qd|^2,  l_T = w_ee |ee(q) - target|^2 + w_vT |qd|^2
- *   QUAD18 (base joints Px Py Pz Rz Ry Rx, legs attached to body 5):
+ *   QUAD18 (compiled for this tree, others rejected with TO_ERR_ARG: base
+ *     joints Px Py Pz Rz Ry Rx as the chain of bodies 0..5, then four legs
+ *     of three bodies each -- hip Rx on body 5, thigh Ry, calf Ry -- with
+ *     foot f on the calf, body 8 + 3 f):
  *     [C] w_tau [C+1] z_nom [C+2] w_z [C+3] w_rpy [C+4] w_vx [C+5] vx target
  *     [C+6] terminal scale [C+7] contact stiffness k [C+8] damping d
  *     [C+9] softplus beta [C+10] n_feet (4) then per foot: body, point (3)

@@ -9,12 +9,21 @@
 
 namespace to {
 
-template <int N>
+// The device model is compiled for one joint tree per system (RigidTopo):
+// the parameters must describe exactly that tree.
+template <int KIND, int N>
 inline bool fill_rigid(const RigidHeader& h, int a0, RigidParams<double, N>& P, std::string& err) {
   if (h.N != N || h.a0 != a0) {
     err = "rigid params: this system needs N=" + std::to_string(N) + ", a0=" + std::to_string(a0);
     return false;
   }
+  typedef RigidTopo<KIND> Topo;
+  for (int i = 0; i < N; ++i)
+    if (h.bodies[i].parent != Topo::parent(i) || h.bodies[i].jtype != Topo::jtype(i)) {
+      err = "rigid params: body " + std::to_string(i) + " must have parent " + std::to_string(Topo::parent(i)) +
+            " and joint type " + std::to_string(Topo::jtype(i)) + " (the system's joint tree)";
+      return false;
+    }
   P.dt = h.dt;
   for (int k = 0; k < 3; ++k) P.g[k] = h.g[k];
   P.n_sub = h.n_sub;

@@ -10,12 +10,7 @@ static int parse_arm7(const double* p, size_t np, std::vector<unsigned char>& bl
   RigidHeader h;
   if (!parse_rigid(p, np, h, err)) return -1;
   RigidParams<double, 7> P{};
-  if (!fill_rigid<7>(h, 0, P, err)) return -1;
-  for (int i = 0; i < 7; ++i)
-    if (h.bodies[i].parent != i - 1 || h.bodies[i].jtype > 2) {
-      err = "arm7 params: joints must be a chain of revolute joints";
-      return -1;
-    }
+  if (!fill_rigid<RK_ARM7, 7>(h, 0, P, err)) return -1;
   if (h.n_cost < 11) { err = "arm7 params: cost block truncated"; return -1; }
   const double* c = h.cost;
   P.wtau = c[0]; P.wv = c[1];
@@ -23,7 +18,7 @@ static int parse_arm7(const double* p, size_t np, std::vector<unsigned char>& bl
   P.wee = c[5]; P.wvT = c[6];
   P.ee_body = (int)c[7];
   P.ee_pt[0] = c[8]; P.ee_pt[1] = c[9]; P.ee_pt[2] = c[10];
-  if (P.ee_body < 0 || P.ee_body >= 7) { err = "arm7 params: bad end-effector body"; return -1; }
+  if (P.ee_body != RigidTopo<RK_ARM7>::kEeBody) { err = "arm7 params: the end effector must be on body 6"; return -1; }
   P.nfeet = 0;
   to_blobs<RigidArm7P>(P, blob64, blob32);
   return 0;

@@ -10,19 +10,19 @@ static int parse_quad(const double* p, size_t np, std::vector<unsigned char>& bl
   RigidHeader h;
   if (!parse_rigid(p, np, h, err)) return -1;
   RigidParams<double, 18> P{};
-  if (!fill_rigid<18>(h, 6, P, err)) return -1;
+  if (!fill_rigid<RK_QUAD, 18>(h, 6, P, err)) return -1;
   if (h.n_cost < 11) { err = "quad params: cost block truncated"; return -1; }
   const double* c = h.cost;
   P.wtau = c[0]; P.znom = c[1]; P.wz = c[2]; P.wrpy = c[3]; P.wvx = c[4]; P.vxt = c[5];
   P.tscale = c[6]; P.kc = c[7]; P.dc = c[8]; P.beta = c[9];
   P.nfeet = (int)c[10];
-  if (P.nfeet < 0 || P.nfeet > 4 || h.n_cost < (size_t)(11 + 4 * P.nfeet) || !(P.beta > 0)) {
-    err = "quad params: bad contact block";
+  if (P.nfeet != RigidTopo<RK_QUAD>::kFeet || h.n_cost < (size_t)(11 + 4 * P.nfeet) || !(P.beta > 0)) {
+    err = "quad params: bad contact block (four feet)";
     return -1;
   }
   for (int f = 0; f < P.nfeet; ++f) {
     P.foot_body[f] = (int)c[11 + 4 * f];
-    if (P.foot_body[f] < 0 || P.foot_body[f] >= 18) { err = "quad params: bad foot body"; return -1; }
+    if (P.foot_body[f] != RigidTopo<RK_QUAD>::foot_body(f)) { err = "quad params: foot f must be on calf body 8 + 3 f"; return -1; }
     for (int k = 0; k < 3; ++k) P.foot_pt[f][k] = c[12 + 4 * f + k];
   }
   to_blobs<RigidQuadP>(P, blob64, blob32);

@@ -86,6 +86,7 @@ inline void cast_params(const RigidParams<S, N>& s, RigidParams<D, N>& d) {
   d.dt = (D)s.dt;
   for (int k = 0; k < 3; ++k) { d.g[k] = (D)s.g[k]; d.tgt[k] = (D)s.tgt[k]; d.ee_pt[k] = (D)s.ee_pt[k]; }
   d.n_sub = s.n_sub; d.a0 = s.a0;
+  #pragma unroll
   for (int i = 0; i < N; ++i) {
     d.parent[i] = s.parent[i]; d.jtype[i] = s.jtype[i]; d.mass[i] = (D)s.mass[i];
     for (int k = 0; k < 3; ++k) { d.off[i][k] = (D)s.off[i][k]; d.com[i][k] = (D)s.com[i][k]; d.inertia[i][k] = (D)s.inertia[i][k]; }
@@ -100,6 +101,43 @@ inline void cast_params(const RigidParams<S, N>& s, RigidParams<D, N>& d) {
 }
 
 // ---------------------------------------------------------------------------
+// Joint trees, fixed at compile time: every loop over the bodies and over an
+// ancestor chain has a compile-time trip count and unrolls, so the per-body
+// arrays of the recursions are registers (or fixed stack slots) rather than
+// dynamically indexed local memory.  parent(i) < i (parents first); depth(i)
+// counts the ancestors of body i and anc(i, d) is its d-th ancestor
+// (anc(i, 0) = i).  Joint types: 0..2 revolute about x, y, z; 3..5 prismatic
+// along x, y, z.  The host parser accepts exactly these trees.
+// ---------------------------------------------------------------------------
+template <int KIND>
+struct RigidTopo;
+
+// 7-DoF arm: a chain of revolute joints about z, y, z, y, z, y, z; the end
+// effector on the last body
+template <>
+struct RigidTopo<RK_ARM7> {
+  static constexpr int kBodies = 7, kDepthMax = 6, kFeet = 0, kEeBody = 6;
+  static constexpr int parent(int i) { return i - 1; }
+  static constexpr int jtype(int i) { return (i & 1) ? 1 : 2; }
+  static constexpr int depth(int i) { return i; }
+  static constexpr int anc(int i, int d) { return i - d; }
+  static constexpr int foot_body(int) { return -1; }
+};
+
+// quadruped: the floating base as the chain Px, Py, Pz, Rz, Ry, Rx (bodies
+// 0..5, the base's mass on body 5), then four legs of hip (x), thigh (y) and
+// calf (y) joints hanging from body 5; the feet on the calves
+template <>
+struct RigidTopo<RK_QUAD> {
+  static constexpr int kBodies = 18, kDepthMax = 8, kFeet = 4, kEeBody = -1;
+  static constexpr int parent(int i) { return i < 6 ? i - 1 : ((i - 6) % 3 == 0 ? 5 : i - 1); }
+  static constexpr int jtype(int i) { return i < 3 ? 3 + i : (i < 6 ? 5 - i : ((i - 6) % 3 == 0 ? 0 : 1)); }
+  static constexpr int depth(int i) { return i < 6 ? i : 6 + (i - 6) % 3; }
+  static constexpr int anc(int i, int d) { return (i < 6 || d <= (i - 6) % 3) ? i - d : 6 + (i - 6) % 3 - d; }
+  static constexpr int foot_body(int f) { return 8 + 3 * f; }
+};
+
+// ---------------------------------------------------------------------------
 // the model
 // ---------------------------------------------------------------------------
 template <int N_, int A0, int KIND>
@@ -108,6 +146,14 @@ struct SysRigid {
   static constexpr int n = 2 * N, m = N - A0;
   static constexpr bool kActor = (KIND == RK_QUAD);   // 36 -> 256 -> 256 -> 12 actor warm start
   template <class R> using ParamsT = RigidParams<R, N>;
+  typedef RigidTopo<KIND> Topo;
+  static_assert(Topo::kBodies == N, "joint tree size");
+  static constexpr int kDepthMax = Topo::kDepthMax, kFeet = Topo::kFeet, kEeBody = Topo::kEeBody;
+  static constexpr int parent(int i) { return Topo::parent(i); }
+  static constexpr int jtype(int i) { return Topo::jtype(i); }
+  static constexpr int depth(int i) { return Topo::depth(i); }
+  static constexpr int anc(int i, int d) { return Topo::anc(i, d); }
+  static constexpr int foot_body(int f) { return Topo::foot_body(f); }
 
   // 3-vectors
   template <class S> TO_DEV static void cross(const S* a, const S* b, S* c) {
@@ -130,11 +176,9 @@ struct SysRigid {
 
   // y = E x and y = E^T x for a joint transform: a rotation about the joint's
   // coordinate axis (4 nonzeros besides the unit entry) or the identity
-  // (prismatic); the joint type is the same on every lane at a given body.
-  // The sparse form pays in float64 (each FP64 instruction is costly on this
-  // part); in float32 the branch-free dense product measured faster.
+  // (prismatic).  The joint type is a compile-time constant at every call
+  // (the body loops unroll), so the switch folds away.
   template <class S> TO_DEV static void jmv(int jt, const S* E, const S* x, S* y) {
-    if constexpr (sizeof(S) == 4) { mv(E, x, y); return; }
     const S x0 = x[0], x1 = x[1], x2 = x[2];
     switch (jt) {
       case 0: { const S c = E[4], s = E[5]; y[0] = x0; y[1] = c * x1 + s * x2; y[2] = c * x2 - s * x1; break; }
@@ -144,7 +188,6 @@ struct SysRigid {
     }
   }
   template <class S> TO_DEV static void jmtv(int jt, const S* E, const S* x, S* y) {
-    if constexpr (sizeof(S) == 4) { mtv(E, x, y); return; }
     const S x0 = x[0], x1 = x[1], x2 = x[2];
     switch (jt) {
       case 0: { const S c = E[4], s = E[5]; y[0] = x0; y[1] = c * x1 - s * x2; y[2] = c * x2 + s * x1; break; }
@@ -159,7 +202,7 @@ struct SysRigid {
   // body origin in parent coordinates
   template <class R, class S>
   TO_DEV static void joint_transform(const ParamsT<R>& P, int i, S q, S* E, S* r) {
-    const int jt = P.jtype[i];
+    const int jt = jtype(i);
 #pragma unroll
     for (int k = 0; k < 3; ++k) r[k] = S(P.off[i][k]);
 #pragma unroll
@@ -180,10 +223,11 @@ struct SysRigid {
   // world pose: E0 maps world to body coordinates, p0 is the body origin
   template <class R, class S>
   TO_DEV static void world_pose(const ParamsT<R>& P, const S* q, S (*E0)[9], S (*p0)[3]) {
+    #pragma unroll
     for (int i = 0; i < N; ++i) {
       S E[9], r[3];
       joint_transform(P, i, q[i], E, r);
-      const int pa = P.parent[i];
+      const int pa = parent(i);
       if (pa < 0) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) E0[i][k] = E[k];
@@ -228,9 +272,10 @@ struct SysRigid {
     S aw[3], av[3];
     S E0[KIND == RK_QUAD ? N : 1][9], p0[KIND == RK_QUAD ? N : 1][3];
     S awb[N][3], avb[N][3];
+    #pragma unroll
     for (int i = 0; i < N; ++i) {
       joint_transform(P, i, q[i], E[i], r[i]);
-      const int pa = P.parent[i];
+      const int pa = parent(i);
       S pw[3], pv[3], paw[3], pav[3];
       if (pa < 0) {
 #pragma unroll
@@ -249,15 +294,15 @@ struct SysRigid {
       cross(r[i], pw, rw);
 #pragma unroll
       for (int k = 0; k < 3; ++k) t[k] = pv[k] - rw[k];
-      jmv(P.jtype[i], E[i], pw, vw[i]);
-      jmv(P.jtype[i], E[i], t, vv[i]);
+      jmv(jtype(i), E[i], pw, vw[i]);
+      jmv(jtype(i), E[i], t, vv[i]);
       cross(r[i], paw, rw);
 #pragma unroll
       for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
-      jmv(P.jtype[i], E[i], paw, aw);
-      jmv(P.jtype[i], E[i], t, av);
+      jmv(jtype(i), E[i], paw, aw);
+      jmv(jtype(i), E[i], t, av);
       // joint motion S qd, S qdd; velocity-product term v x (S qd)
-      const int jt = P.jtype[i];
+      const int jt = jtype(i);
       S sw[3] = {S(R(0)), S(R(0)), S(R(0))}, sv[3] = {S(R(0)), S(R(0)), S(R(0))};
       if (jt <= 2) sw[jt] = qd[i]; else sv[jt - 3] = qd[i];
 #pragma unroll
@@ -301,8 +346,9 @@ struct SysRigid {
       }
     }
     if (KIND == RK_QUAD && contact) {
-      for (int ft = 0; ft < P.nfeet; ++ft) {
-        const int bi = P.foot_body[ft];
+      #pragma unroll
+      for (int ft = 0; ft < kFeet; ++ft) {
+        const int bi = foot_body(ft);
         S pt[3] = {S(P.foot_pt[ft][0]), S(P.foot_pt[ft][1]), S(P.foot_pt[ft][2])};
         S wpt[3], Pw[3], wxp[3], vb[3], vwld[3];
         mtv(E0[bi], pt, wpt);
@@ -338,10 +384,11 @@ struct SysRigid {
         for (int k = 0; k < 3; ++k) { fn[bi][k] = fn[bi][k] - mb[k]; ff[bi][k] = ff[bi][k] - fb[k]; }
       }
     }
+    #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
-      const int jt = P.jtype[i];
+      const int jt = jtype(i);
       tau[i] = jt <= 2 ? fn[i][jt] : ff[i][jt - 3];
-      const int pa = P.parent[i];
+      const int pa = parent(i);
       if (pa >= 0) {
         // X^T f = (E^T n + r x E^T f, E^T f)
         S en[3], ef[3], rf[3];
@@ -365,6 +412,7 @@ struct SysRigid {
   TO_DEV static void mass_chol(const ParamsT<R>& P, const R* q, R* L) {
     R E[N][9], r[N][3];
     R cm[N], ch[N][3], cI[N][6];   // cI: xx, yy, zz, xy, xz, yz
+    #pragma unroll
     for (int i = 0; i < N; ++i) {
       joint_transform(P, i, q[i], E[i], r[i]);
       const R mi = P.mass[i], c0 = P.com[i][0], c1 = P.com[i][1], c2 = P.com[i][2];
@@ -376,15 +424,16 @@ struct SysRigid {
       cI[i][2] = P.inertia[i][2] + mi * (c0 * c0 + c1 * c1);
       cI[i][3] = -mi * c0 * c1; cI[i][4] = -mi * c0 * c2; cI[i][5] = -mi * c1 * c2;
     }
+    #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
-      const int pa = P.parent[i];
+      const int pa = parent(i);
       if (pa < 0) continue;
       const R* e = E[i];
       const R* rr = r[i];
       const R mi = cm[i];
       // h_A = E^T h (parent coordinates, about the child origin)
       R hA[3];
-      jmtv(P.jtype[i], e, ch[i], hA);
+      jmtv(jtype(i), e, ch[i], hA);
       // I_A = E^T I E
       const R I3[9] = {cI[i][0], cI[i][3], cI[i][4], cI[i][3], cI[i][1], cI[i][5], cI[i][4], cI[i][5], cI[i][2]};
       R T[9];   // I E
@@ -410,10 +459,11 @@ struct SysRigid {
       cm[pa] += mi;
     }
     // only (body, ancestor) entries are formed and read: the others are zero
+    #pragma unroll
     for (int i = 0; i < N; ++i) {
       // F = Ic_i S_i: revolute about axis a: (I e_a, e_a x h); prismatic along a: (h x e_a, m e_a)
       R fn[3], ff[3];
-      const int jt = P.jtype[i];
+      const int jt = jtype(i);
       const R* c6 = cI[i];
       if (jt <= 2) {
         const int a = jt;
@@ -431,30 +481,39 @@ struct SysRigid {
         ff[a] = cm[i];
       }
       L[i * N + i] = jt <= 2 ? fn[jt] : ff[jt - 3];
-      int j = i;
-      while (P.parent[j] >= 0) {
-        // force to the parent frame: f_p = E^T f, n_p = E^T n + r x f_p
+#pragma unroll
+      for (int d = 0; d < kDepthMax; ++d) {
+        if (d >= depth(i)) continue;
+        // force across joint j into its parent's frame: f_p = E^T f, n_p = E^T n + r x f_p
+        const int j = anc(i, d), jp = anc(i, d + 1);
         R en[3], ef[3], rf[3];
-        jmtv(P.jtype[j], E[j], fn, en);
-        jmtv(P.jtype[j], E[j], ff, ef);
+        jmtv(jtype(j), E[j], fn, en);
+        jmtv(jtype(j), E[j], ff, ef);
         cross(r[j], ef, rf);
 #pragma unroll
         for (int k = 0; k < 3; ++k) { fn[k] = en[k] + rf[k]; ff[k] = ef[k]; }
-        j = P.parent[j];
-        const int jj = P.jtype[j];
-        L[i * N + j] = jj <= 2 ? fn[jj] : ff[jj - 3];
+        const int jj = jtype(jp);
+        L[i * N + jp] = jj <= 2 ? fn[jj] : ff[jj - 3];
       }
     }
     // M = L^T L with L lower triangular and the tree's sparsity (Featherstone
     // 2008, Sec. 6.5): eliminating from the last body up touches only
     // (body, ancestor) pairs, so nothing fills in; 1 / L_kk on the diagonal
+#pragma unroll
     for (int k = N - 1; k >= 0; --k) {
       const R rk = rsqrt_(L[k * N + k]);
       L[k * N + k] = rk;
-      for (int i = P.parent[k]; i >= 0; i = P.parent[i]) L[k * N + i] *= rk;
-      for (int i = P.parent[k]; i >= 0; i = P.parent[i]) {
+#pragma unroll
+      for (int d = 1; d <= kDepthMax; ++d)
+        if (d <= depth(k)) L[k * N + anc(k, d)] *= rk;
+#pragma unroll
+      for (int d = 1; d <= kDepthMax; ++d) {
+        if (d > depth(k)) continue;
+        const int i = anc(k, d);
         const R lki = L[k * N + i];
-        for (int j = i; j >= 0; j = P.parent[j]) L[i * N + j] -= lki * L[k * N + j];
+#pragma unroll
+        for (int e = 0; e <= kDepthMax; ++e)
+          if (e <= depth(i)) L[i * N + anc(i, e)] -= lki * L[k * N + anc(i, e)];
       }
     }
   }
@@ -463,14 +522,21 @@ struct SysRigid {
   template <class R>
   TO_DEV static void chol_solve(const ParamsT<R>& P, const R* L, const R* b, R* x) {
     R y[N];
+#pragma unroll
     for (int i = 0; i < N; ++i) y[i] = b[i];
+#pragma unroll
     for (int k = N - 1; k >= 0; --k) {
       y[k] *= L[k * N + k];
-      for (int i = P.parent[k]; i >= 0; i = P.parent[i]) y[i] -= L[k * N + i] * y[k];
+#pragma unroll
+      for (int d = 1; d <= kDepthMax; ++d)
+        if (d <= depth(k)) y[anc(k, d)] -= L[k * N + anc(k, d)] * y[k];
     }
+#pragma unroll
     for (int k = 0; k < N; ++k) {
       R t = y[k];
-      for (int i = P.parent[k]; i >= 0; i = P.parent[i]) t -= L[k * N + i] * x[i];
+#pragma unroll
+      for (int d = 1; d <= kDepthMax; ++d)
+        if (d <= depth(k)) t -= L[k * N + anc(k, d)] * x[anc(k, d)];
       x[k] = t * L[k * N + k];
     }
   }
@@ -479,9 +545,11 @@ struct SysRigid {
   template <class R>
   TO_DEV static void accel(const ParamsT<R>& P, const R* q, const R* qd, const R* tau, R* qdd, R* L) {
     R z[N], h[N], rhs[N];
+    #pragma unroll
     for (int i = 0; i < N; ++i) z[i] = R(0);
     rnea<R, R>(P, q, qd, z, true, KIND == RK_QUAD, h);
     mass_chol(P, q, L);
+    #pragma unroll
     for (int i = 0; i < N; ++i) rhs[i] = tau[i] - h[i];
     chol_solve(P, L, rhs, qdd);
   }
@@ -492,7 +560,7 @@ struct SysRigid {
   TO_DEV static void ee_world(const ParamsT<R>& P, const S* q, S* ee) {
     S E0[N][9], p0[N][3];
     world_pose(P, q, E0, p0);
-    const int b = P.ee_body;
+    const int b = kEeBody < 0 ? 0 : kEeBody;   // the arm's end-effector body (unused for the quadruped)
     S pt[3] = {S(P.ee_pt[0]), S(P.ee_pt[1]), S(P.ee_pt[2])}, w[3];
     mtv(E0[b], pt, w);
 #pragma unroll
@@ -504,6 +572,7 @@ struct SysRigid {
     R l = 0;
     for (int j = 0; j < m; ++j) l += P.wtau * u[j] * u[j];
     if (KIND == RK_ARM7) {
+      #pragma unroll
       for (int j = 0; j < N; ++j) l += P.wv * x[N + j] * x[N + j];
     } else {
       const R dz = x[2] - P.znom, dv = x[N] - P.vxt;
@@ -516,6 +585,7 @@ struct SysRigid {
   TO_DEV static R cost_step2(const ParamsT<R>& P, R* xh, R* xl, const R* u) {
     const R l = running_cost(P, xh, u);
     R tau[N], qdd[N], L[N * N];
+    #pragma unroll
     for (int i = 0; i < N; ++i) tau[i] = i < A0 ? R(0) : u[i - A0];
     const R h = P.dt / (R)P.n_sub;
     for (int s = 0; s < P.n_sub; ++s) {
@@ -531,6 +601,7 @@ struct SysRigid {
       R ee[3];
       ee_world(P, x, ee);
       for (int k = 0; k < 3; ++k) { const R d = ee[k] - P.tgt[k]; l += P.wee * d * d; }
+      #pragma unroll
       for (int j = 0; j < N; ++j) l += P.wvT * x[N + j] * x[N + j];
     } else {
       const R dz = x[2] - P.znom, dv = x[N] - P.vxt;
@@ -552,6 +623,7 @@ struct SysRigid {
     for (int i = 0; i < n; ++i) lxx[i * n + i] = clip0(eps);
     if (KIND == RK_ARM7) {
       const R v2 = R(2) * P.wv;
+      #pragma unroll
       for (int j = 0; j < N; ++j) { lx[N + j] = v2 * x[N + j]; lxx[(N + j) * n + N + j] = v2 > eps ? v2 : eps; }
     } else {
       const R z2 = R(2) * P.wz, r2 = R(2) * P.wrpy, x2 = R(2) * P.wvx;
@@ -575,6 +647,7 @@ struct SysRigid {
       for (int a = 0; a < N; ++a)
         for (int b = a; b < N; ++b) {
           H q[N];
+          #pragma unroll
           for (int k = 0; k < N; ++k) q[k] = H(Dl<R>(x[k], k == a ? R(1) : R(0)), Dl<R>(k == b ? R(1) : R(0), R(0)));
           H ee[3];
           ee_world(P, q, ee);
@@ -592,6 +665,7 @@ struct SysRigid {
       for (int a = 0; a < N; ++a)
         for (int b = 0; b < N; ++b) lxx[a * n + b] = Q[a * N + b];
       const R v2 = R(2) * P.wvT;
+      #pragma unroll
       for (int j = 0; j < N; ++j) { lx[N + j] = v2 * x[N + j]; lxx[(N + j) * n + N + j] = v2 > eps ? v2 : eps; }
     } else {
       const R s = P.tscale;
@@ -653,9 +727,10 @@ struct SysRigid {
   TO_DEV static void rnea_store(const ParamsT<R>& P, Prim<R>& pr) {
     R (*aw)[3] = pr.aw;
     R av[N][3];
+    #pragma unroll
     for (int i = 0; i < N; ++i) {
       joint_transform(P, i, pr.q[i], pr.E[i], pr.r[i]);
-      const int pa = P.parent[i];
+      const int pa = parent(i);
       R pw[3], pv[3], paw[3], pav[3];
       for (int k = 0; k < 3; ++k) {
         pw[k] = pa < 0 ? R(0) : pr.vw[pa][k];
@@ -668,13 +743,13 @@ struct SysRigid {
       R t[3], rw[3];
       cross(r, pw, rw);
       for (int k = 0; k < 3; ++k) t[k] = pv[k] - rw[k];
-      jmv(P.jtype[i], E, pw, pr.Epw[i]);
-      jmv(P.jtype[i], E, t, pr.Ept[i]);
+      jmv(jtype(i), E, pw, pr.Epw[i]);
+      jmv(jtype(i), E, t, pr.Ept[i]);
       cross(r, paw, rw);
       for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
-      jmv(P.jtype[i], E, paw, pr.Epa[i]);
-      jmv(P.jtype[i], E, t, pr.Epb[i]);
-      const int jt = P.jtype[i];
+      jmv(jtype(i), E, paw, pr.Epa[i]);
+      jmv(jtype(i), E, t, pr.Epb[i]);
+      const int jt = jtype(i);
       R sw[3] = {R(0), R(0), R(0)}, sv[3] = {R(0), R(0), R(0)};
       if (jt <= 2) sw[jt] = pr.qd[i]; else sv[jt - 3] = pr.qd[i];
       for (int k = 0; k < 3; ++k) { pr.vw[i][k] = pr.Epw[i][k] + sw[k]; pr.vv[i][k] = pr.Ept[i][k] + sv[k]; }
@@ -705,8 +780,9 @@ struct SysRigid {
       }
     }
     if (KIND == RK_QUAD) {
-      for (int ft = 0; ft < P.nfeet; ++ft) {
-        const int bi = P.foot_body[ft];
+      #pragma unroll
+      for (int ft = 0; ft < kFeet; ++ft) {
+        const int bi = foot_body(ft);
         const R pt[3] = {P.foot_pt[ft][0], P.foot_pt[ft][1], P.foot_pt[ft][2]};
         mtv(pr.E0[bi], pt, pr.wpt[ft]);
         R wxp[3];
@@ -736,10 +812,11 @@ struct SysRigid {
         for (int k = 0; k < 3; ++k) { pr.fn[bi][k] -= mb[k]; pr.ff[bi][k] -= fb[k]; }
       }
     }
+    #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
-      const int jt = P.jtype[i];
+      const int jt = jtype(i);
       pr.tau[i] = jt <= 2 ? pr.fn[i][jt] : pr.ff[i][jt - 3];
-      const int pa = P.parent[i];
+      const int pa = parent(i);
       if (pa >= 0) {
         R en[3], ef[3], rf[3];
         jmtv(jt, pr.E[i], pr.fn[i], en);
@@ -759,9 +836,10 @@ struct SysRigid {
   TO_DEV static void rnea_tangent(const ParamsT<R>& P, const Prim<R>& pr, const R* dq, const R* dqd, R* dtau) {
     R dvw[N][3], dvv[N][3], daw[N][3], dav[N][3], dfn[N][3], dff[N][3];
     R dE0[KIND == RK_QUAD ? N : 1][9], dp0[KIND == RK_QUAD ? N : 1][3];
+    #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const int pa = P.parent[i];
-      const int jt = P.jtype[i];
+      const int pa = parent(i);
+      const int jt = jtype(i);
       const bool rev = jt <= 2;
       const int ax = rev ? jt : jt - 3;
       const R sq = rev ? dq[i] : R(0);          // rotation tangent
@@ -846,8 +924,9 @@ struct SysRigid {
       }
     }
     if (KIND == RK_QUAD) {
-      for (int ft = 0; ft < P.nfeet; ++ft) {
-        const int bi = P.foot_body[ft];
+      #pragma unroll
+      for (int ft = 0; ft < kFeet; ++ft) {
+        const int bi = foot_body(ft);
         const R pt[3] = {P.foot_pt[ft][0], P.foot_pt[ft][1], P.foot_pt[ft][2]};
         const R* E0 = pr.E0[bi];
         R dwpt[3], dvb[3], dvwld[3], w1[3];
@@ -878,12 +957,13 @@ struct SysRigid {
         for (int k = 0; k < 3; ++k) { dfn[bi][k] -= dmb[k]; dff[bi][k] -= dfb[k]; }
       }
     }
+    #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
-      const int jt = P.jtype[i];
+      const int jt = jtype(i);
       const bool rev = jt <= 2;
       const int ax = rev ? jt : jt - 3;
       dtau[i] = rev ? dfn[i][ax] : dff[i][ax];
-      const int pa = P.parent[i];
+      const int pa = parent(i);
       if (pa >= 0) {
         // d(E^T y) = E^T dy + dq E^T (e_ax x y) for a revolute joint
         const R* E = pr.E[i];
@@ -924,11 +1004,13 @@ struct SysRigid {
     const int c = g.lane;
     const bool dir = c < n + m;
     R dq[N], dqd[N];
+    #pragma unroll
     for (int i = 0; i < N; ++i) {
       dq[i] = (c == i) ? R(1) : R(0);
       dqd[i] = (c == N + i) ? R(1) : R(0);
     }
     if (c == 0)
+      #pragma unroll
       for (int i = 0; i < N; ++i) { pr.q[i] = x[i]; pr.qd[i] = x[N + i]; pr.tin[i] = i < A0 ? R(0) : u[i - A0]; }
     const R h = P.dt / (R)P.n_sub;
     for (int s = 0; s < P.n_sub; ++s) {
@@ -940,8 +1022,10 @@ struct SysRigid {
       if (dir) {
         R dtau[N], rhs[N], dqdd[N];
         rnea_tangent(P, pr, dq, dqd, dtau);
+        #pragma unroll
         for (int i = 0; i < N; ++i) rhs[i] = ((c >= n && i == A0 + (c - n)) ? R(1) : R(0)) - dtau[i];
         chol_solve(P, pr.L, rhs, dqdd);
+        #pragma unroll
         for (int i = 0; i < N; ++i) {
           dqd[i] = dqd[i] + h * dqdd[i];
           dq[i] = dq[i] + h * dqd[i];
@@ -949,6 +1033,7 @@ struct SysRigid {
       }
       g.sync();
       if (c == 0)
+        #pragma unroll
         for (int i = 0; i < N; ++i) {
           pr.qd[i] = pr.qd[i] + h * pr.qdd[i];
           pr.q[i] = pr.q[i] + h * pr.qd[i];
@@ -956,8 +1041,10 @@ struct SysRigid {
     }
     if (dir) {
       if (c < n) {
+        #pragma unroll
         for (int i = 0; i < N; ++i) { A[i * n + c] = dq[i]; A[(N + i) * n + c] = dqd[i]; }
       } else {
+        #pragma unroll
         for (int i = 0; i < N; ++i) { B[i * m + (c - n)] = dq[i]; B[(N + i) * m + (c - n)] = dqd[i]; }
       }
     }
