@@ -190,6 +190,13 @@ struct Solver {
   static constexpr int LW = G < kLsWidth ? G : kLsWidth;   // step sizes per line-search round
   static constexpr int NS = LW + 1;                        // trajectory slots per knot
   static constexpr int kRounds = (kMaxAlpha + LW - 1) / LW; // most line-search rounds
+  // a system whose rollout step is shared by partner lanes has a slot for
+  // every line-search lane
+  template <class S> static constexpr bool step_slots_fit() {
+    if constexpr (S::template kGroupStep<G>) return LW <= S::kStepSlots;
+    else return true;
+  }
+  static_assert(step_slots_fit<Sys>(), "line-search lanes exceed the system's step slots");
   typedef typename Sys::template ParamsT<R> Params;
   static constexpr bool kLane = (G == 1);                  // one thread per instance, matrices in registers
   typedef std::conditional_t<kLane, WorkLane, Work<Sys, R>> W;
@@ -1001,8 +1008,8 @@ struct Solver {
                 actor_mlp(g, w, run, a.actor_w);
               }
             }
+            R uh[m];
             if (act && mine) {
-              R uh[m];
               if (mode == M_NEW) {
                 bool from_actor = false;
                 if constexpr (Sys::kActor) {
@@ -1021,7 +1028,13 @@ struct Solver {
               }
               // the padding too: whole 32-byte sectors reach L2 without a read
               put_record(rec(traj, base, k, slot), xh, uh, xlo);
-              Jc.add(Sys::cost_step2(P, xh, xlo, uh));
+              if constexpr (!Sys::template kGroupStep<G>) Jc.add(Sys::cost_step2(P, xh, xlo, uh));
+            }
+            if constexpr (Sys::template kGroupStep<G>) {
+              // the system's step is shared by partner lanes (group barriers inside;
+              // act is uniform over a CTA-wide group)
+              const R l = Sys::template cost_step_group<R, G>(P, g, act && mine, xh, xlo, uh, w.sx);
+              if (act && mine) Jc.add(l);
             }
             if constexpr (!kLane) g.sync();
           }

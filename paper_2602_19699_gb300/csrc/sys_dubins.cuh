@@ -29,6 +29,7 @@ struct SysDubins {
   static constexpr bool kActor = false;
   template <class R> using ParamsT = DubinsParams<R>;
   template <class R> struct Scratch { static constexpr int elems = 1; };
+  template <int G> static constexpr bool kGroupStep = false;
 
 
   template <class R>

@@ -45,6 +45,7 @@ struct SysPlanar3 {
   static constexpr bool kActor = false;
   template <class R> using ParamsT = Planar3Params<R>;
   template <class R> struct Scratch { static constexpr int elems = 1; };
+  template <int G> static constexpr bool kGroupStep = false;
 
   // absolute link angles, link and centre-of-mass vectors, joint positions
   template <class R>

@@ -25,6 +25,7 @@ struct SysPointMass {
   static constexpr bool kActor = false;
   template <class R> using ParamsT = PointMassParams<R>;
   template <class R> struct Scratch { static constexpr int elems = 1; };
+  template <int G> static constexpr bool kGroupStep = false;
 
 
   template <class R>

@@ -86,7 +86,7 @@ inline void cast_params(const RigidParams<S, N>& s, RigidParams<D, N>& d) {
   d.dt = (D)s.dt;
   for (int k = 0; k < 3; ++k) { d.g[k] = (D)s.g[k]; d.tgt[k] = (D)s.tgt[k]; d.ee_pt[k] = (D)s.ee_pt[k]; }
   d.n_sub = s.n_sub; d.a0 = s.a0;
-  #pragma unroll
+#pragma unroll
   for (int i = 0; i < N; ++i) {
     d.parent[i] = s.parent[i]; d.jtype[i] = s.jtype[i]; d.mass[i] = (D)s.mass[i];
     for (int k = 0; k < 3; ++k) { d.off[i][k] = (D)s.off[i][k]; d.com[i][k] = (D)s.com[i][k]; d.inertia[i][k] = (D)s.inertia[i][k]; }
@@ -223,7 +223,7 @@ struct SysRigid {
   // world pose: E0 maps world to body coordinates, p0 is the body origin
   template <class R, class S>
   TO_DEV static void world_pose(const ParamsT<R>& P, const S* q, S (*E0)[9], S (*p0)[3]) {
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) {
       S E[9], r[3];
       joint_transform(P, i, q[i], E, r);
@@ -272,7 +272,7 @@ struct SysRigid {
     S aw[3], av[3];
     S E0[KIND == RK_QUAD ? N : 1][9], p0[KIND == RK_QUAD ? N : 1][3];
     S awb[N][3], avb[N][3];
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) {
       joint_transform(P, i, q[i], E[i], r[i]);
       const int pa = parent(i);
@@ -346,7 +346,7 @@ struct SysRigid {
       }
     }
     if (KIND == RK_QUAD && contact) {
-      #pragma unroll
+#pragma unroll
       for (int ft = 0; ft < kFeet; ++ft) {
         const int bi = foot_body(ft);
         S pt[3] = {S(P.foot_pt[ft][0]), S(P.foot_pt[ft][1]), S(P.foot_pt[ft][2])};
@@ -384,7 +384,7 @@ struct SysRigid {
         for (int k = 0; k < 3; ++k) { fn[bi][k] = fn[bi][k] - mb[k]; ff[bi][k] = ff[bi][k] - fb[k]; }
       }
     }
-    #pragma unroll
+#pragma unroll
     for (int i = N - 1; i >= 0; --i) {
       const int jt = jtype(i);
       tau[i] = jt <= 2 ? fn[i][jt] : ff[i][jt - 3];
@@ -412,7 +412,7 @@ struct SysRigid {
   TO_DEV static void mass_chol(const ParamsT<R>& P, const R* q, R* L) {
     R E[N][9], r[N][3];
     R cm[N], ch[N][3], cI[N][6];   // cI: xx, yy, zz, xy, xz, yz
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) {
       joint_transform(P, i, q[i], E[i], r[i]);
       const R mi = P.mass[i], c0 = P.com[i][0], c1 = P.com[i][1], c2 = P.com[i][2];
@@ -424,7 +424,7 @@ struct SysRigid {
       cI[i][2] = P.inertia[i][2] + mi * (c0 * c0 + c1 * c1);
       cI[i][3] = -mi * c0 * c1; cI[i][4] = -mi * c0 * c2; cI[i][5] = -mi * c1 * c2;
     }
-    #pragma unroll
+#pragma unroll
     for (int i = N - 1; i >= 0; --i) {
       const int pa = parent(i);
       if (pa < 0) continue;
@@ -459,7 +459,7 @@ struct SysRigid {
       cm[pa] += mi;
     }
     // only (body, ancestor) entries are formed and read: the others are zero
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) {
       // F = Ic_i S_i: revolute about axis a: (I e_a, e_a x h); prismatic along a: (h x e_a, m e_a)
       R fn[3], ff[3];
@@ -517,6 +517,24 @@ struct SysRigid {
       }
     }
   }
+  // mass_chol of q held in (shared) memory into (shared) memory: q read once,
+  // the factor formed in registers, then only its tree-sparse entries (the
+  // diagonal and the (body, ancestor) pairs, all that chol_solve reads) stored
+  template <class R>
+  TO_DEV static void mass_chol_mem(const ParamsT<R>& P, const R* qm, R* Lm) {
+    R q[N], L[N * N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) q[i] = qm[i];
+    mass_chol(P, q, L);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      Lm[k * N + k] = L[k * N + k];
+#pragma unroll
+      for (int d = 1; d <= kDepthMax; ++d)
+        if (d <= depth(k)) Lm[k * N + anc(k, d)] = L[k * N + anc(k, d)];
+    }
+  }
+
   // x = M^{-1} b with M = L^T L from mass_chol: L^T y = b from the leaves up,
   // then L x = y from the root down, each along the ancestor chains
   template <class R>
@@ -545,11 +563,11 @@ struct SysRigid {
   template <class R>
   TO_DEV static void accel(const ParamsT<R>& P, const R* q, const R* qd, const R* tau, R* qdd, R* L) {
     R z[N], h[N], rhs[N];
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) z[i] = R(0);
     rnea<R, R>(P, q, qd, z, true, KIND == RK_QUAD, h);
     mass_chol(P, q, L);
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) rhs[i] = tau[i] - h[i];
     chol_solve(P, L, rhs, qdd);
   }
@@ -572,7 +590,7 @@ struct SysRigid {
     R l = 0;
     for (int j = 0; j < m; ++j) l += P.wtau * u[j] * u[j];
     if (KIND == RK_ARM7) {
-      #pragma unroll
+#pragma unroll
       for (int j = 0; j < N; ++j) l += P.wv * x[N + j] * x[N + j];
     } else {
       const R dz = x[2] - P.znom, dv = x[N] - P.vxt;
@@ -585,7 +603,7 @@ struct SysRigid {
   TO_DEV static R cost_step2(const ParamsT<R>& P, R* xh, R* xl, const R* u) {
     const R l = running_cost(P, xh, u);
     R tau[N], qdd[N], L[N * N];
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) tau[i] = i < A0 ? R(0) : u[i - A0];
     const R h = P.dt / (R)P.n_sub;
     for (int s = 0; s < P.n_sub; ++s) {
@@ -594,6 +612,52 @@ struct SysRigid {
     }
     return l;
   }
+  // cost_step2 shared by a candidate lane and its partner (kGroupStep): every
+  // lane of the group calls it, mine on the candidate lanes (all < kStepSlots);
+  // returns the running cost on those.  Two group barriers per substep.
+  template <class R, int G>
+  TO_DEV static R cost_step_group(const ParamsT<R>& P, const Group<G>& g, bool mine, R* xh, R* xl, const R* u,
+                                  R* scratch) {
+    static_assert(kGroupStep<G>, "a partner lane on the other warp");
+    const int c = g.lane;
+    const int slot = c < 32 ? c : c - 32;
+    R* sq = scratch + slot * kStepSlot;       // q of the candidate's substep
+    R* sL = sq + N;                           // the factor of M(q)
+    R* flag = scratch + kStepSlots * kStepSlot;
+    R l = R(0), tau[N];
+    if (mine) {
+      l = running_cost(P, xh, u);
+#pragma unroll
+      for (int i = 0; i < N; ++i) tau[i] = i < A0 ? R(0) : u[i - A0];
+    }
+    if (c < kStepSlots) flag[c] = mine ? R(1) : R(0);
+    const R h = P.dt / (R)P.n_sub;
+    for (int s = 0; s < P.n_sub; ++s) {
+      if (mine)
+#pragma unroll
+        for (int i = 0; i < N; ++i) sq[i] = xh[i];
+      g.sync();
+      R hb[N];
+      if (mine) {
+        R z[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) z[i] = R(0);
+        rnea<R, R>(P, xh, xh + N, z, true, KIND == RK_QUAD, hb);
+      } else if (c >= 32 && slot < kStepSlots && flag[slot] != R(0)) {
+        mass_chol_mem(P, sq, sL);
+      }
+      g.sync();
+      if (mine) {
+        R rhs[N], qdd[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) rhs[i] = tau[i] - hb[i];
+        chol_solve(P, sL, rhs, qdd);
+        semi_implicit2<R, N>(xh, xl, xh + N, xl + N, qdd, h);
+      }
+    }
+    return l;
+  }
+
   template <class R>
   TO_DEV static R terminal_cost(const ParamsT<R>& P, const R* x) {
     R l = 0;
@@ -601,7 +665,7 @@ struct SysRigid {
       R ee[3];
       ee_world(P, x, ee);
       for (int k = 0; k < 3; ++k) { const R d = ee[k] - P.tgt[k]; l += P.wee * d * d; }
-      #pragma unroll
+#pragma unroll
       for (int j = 0; j < N; ++j) l += P.wvT * x[N + j] * x[N + j];
     } else {
       const R dz = x[2] - P.znom, dv = x[N] - P.vxt;
@@ -623,7 +687,7 @@ struct SysRigid {
     for (int i = 0; i < n; ++i) lxx[i * n + i] = clip0(eps);
     if (KIND == RK_ARM7) {
       const R v2 = R(2) * P.wv;
-      #pragma unroll
+#pragma unroll
       for (int j = 0; j < N; ++j) { lx[N + j] = v2 * x[N + j]; lxx[(N + j) * n + N + j] = v2 > eps ? v2 : eps; }
     } else {
       const R z2 = R(2) * P.wz, r2 = R(2) * P.wrpy, x2 = R(2) * P.wvx;
@@ -647,7 +711,7 @@ struct SysRigid {
       for (int a = 0; a < N; ++a)
         for (int b = a; b < N; ++b) {
           H q[N];
-          #pragma unroll
+#pragma unroll
           for (int k = 0; k < N; ++k) q[k] = H(Dl<R>(x[k], k == a ? R(1) : R(0)), Dl<R>(k == b ? R(1) : R(0), R(0)));
           H ee[3];
           ee_world(P, q, ee);
@@ -665,7 +729,7 @@ struct SysRigid {
       for (int a = 0; a < N; ++a)
         for (int b = 0; b < N; ++b) lxx[a * n + b] = Q[a * N + b];
       const R v2 = R(2) * P.wvT;
-      #pragma unroll
+#pragma unroll
       for (int j = 0; j < N; ++j) { lx[N + j] = v2 * x[N + j]; lxx[(N + j) * n + N + j] = v2 > eps ? v2 : eps; }
     } else {
       const R s = P.tscale;
@@ -696,10 +760,19 @@ struct SysRigid {
     R E0[KIND == RK_QUAD ? N : 1][9], p0[KIND == RK_QUAD ? N : 1][3];
     R wpt[NF][3], F[NF][3], vb[NF][3], vwld[NF][3], gate[NF];
   };
-  // the group's shared-memory scratch (the solver reserves it in its work area)
+  // Line search of a 64-lane group: candidate lane c < kStepSlots steps its
+  // rollout with lane c + 32 (the other warp) as its partner, which forms and
+  // factors the mass matrix while lane c runs the bias Newton-Euler pass.
+  // Per candidate the scratch holds its substep's q and the factor.
+  template <int G> static constexpr bool kGroupStep = (KIND == RK_QUAD) && G >= 64;
+  static constexpr int kStepSlots = 16, kStepSlot = N + N * N;
+  // the group's shared-memory scratch (the solver reserves it in its work
+  // area): the derivative primal, or the line search's per-candidate slots
   template <class R>
   struct Scratch {
-    static constexpr int elems = (int)((sizeof(Prim<R>) + sizeof(R) - 1) / sizeof(R));
+    static constexpr int prim = (int)((sizeof(Prim<R>) + sizeof(R) - 1) / sizeof(R));
+    static constexpr int step = KIND == RK_QUAD ? kStepSlots * kStepSlot + kStepSlots : 0;
+    static constexpr int elems = prim > step ? prim : step;
   };
 
   // y += a x b
@@ -721,75 +794,96 @@ struct SysRigid {
     else { y[0] = -z[1]; y[1] = z[0]; y[2] = S(0); }
   }
 
-  // Newton-Euler at the substep's (q, qd, qdd) in pr (gravity, and contact for
-  // the quadruped), keeping every per-body quantity the tangent pass needs.
+  // A substep's primal for the derivative lanes comes in two halves around
+  // the solve for qdd, so that the joint transforms, the velocities, the
+  // world poses and the contact forces are evaluated once (the tangent pass
+  // reads them all from pr):
+  // bias_store (one lane): those quantities, I v, and the inverse dynamics at
+  // qdd = 0 (gravity, velocity products, contact), i.e. the bias torques h.
   template <class R>
-  TO_DEV static void rnea_store(const ParamsT<R>& P, Prim<R>& pr) {
-    R (*aw)[3] = pr.aw;
-    R av[N][3];
-    #pragma unroll
+  TO_DEV static void bias_store(const ParamsT<R>& P, Prim<R>& pr, R* h) {
+    R aw[N][3], av[N][3], fn[N][3], ff[N][3];
+#pragma unroll
     for (int i = 0; i < N; ++i) {
-      joint_transform(P, i, pr.q[i], pr.E[i], pr.r[i]);
-      const int pa = parent(i);
+      const int pa = parent(i), jt = jtype(i);
+      R E[9], r[3];
+      joint_transform(P, i, pr.q[i], E, r);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) pr.E[i][k] = E[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pr.r[i][k] = r[k];
       R pw[3], pv[3], paw[3], pav[3];
+#pragma unroll
       for (int k = 0; k < 3; ++k) {
         pw[k] = pa < 0 ? R(0) : pr.vw[pa][k];
         pv[k] = pa < 0 ? R(0) : pr.vv[pa][k];
         paw[k] = pa < 0 ? R(0) : aw[pa][k];
         pav[k] = pa < 0 ? -P.g[k] : av[pa][k];
       }
-      const R* E = pr.E[i];
-      const R* r = pr.r[i];
-      R t[3], rw[3];
+      R t[3], rw[3], Epw[3], Ept[3];
       cross(r, pw, rw);
+#pragma unroll
       for (int k = 0; k < 3; ++k) t[k] = pv[k] - rw[k];
-      jmv(jtype(i), E, pw, pr.Epw[i]);
-      jmv(jtype(i), E, t, pr.Ept[i]);
-      cross(r, paw, rw);
-      for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
-      jmv(jtype(i), E, paw, pr.Epa[i]);
-      jmv(jtype(i), E, t, pr.Epb[i]);
-      const int jt = jtype(i);
+      jmv(jt, E, pw, Epw);
+      jmv(jt, E, t, Ept);
       R sw[3] = {R(0), R(0), R(0)}, sv[3] = {R(0), R(0), R(0)};
       if (jt <= 2) sw[jt] = pr.qd[i]; else sv[jt - 3] = pr.qd[i];
-      for (int k = 0; k < 3; ++k) { pr.vw[i][k] = pr.Epw[i][k] + sw[k]; pr.vv[i][k] = pr.Ept[i][k] + sv[k]; }
-      for (int k = 0; k < 3; ++k) { aw[i][k] = pr.Epa[i][k]; av[i][k] = pr.Epb[i][k]; }
-      cross_acc(pr.vw[i], sw, aw[i]);
-      cross_acc(pr.vw[i], sv, av[i]);
-      cross_acc(pr.vv[i], sw, av[i]);
-      if (jt <= 2) aw[i][jt] += pr.qdd[i]; else av[i][jt - 3] += pr.qdd[i];
-      R In[3], If[3];
+      R vw[3], vv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        vw[k] = Epw[k] + sw[k];
+        vv[k] = Ept[k] + sv[k];
+        pr.Epw[i][k] = Epw[k]; pr.Ept[i][k] = Ept[k];
+        pr.vw[i][k] = vw[k]; pr.vv[i][k] = vv[k];
+      }
+      // the acceleration at qdd = 0 and the body force it needs
+      cross(r, paw, rw);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
+      jmv(jt, E, paw, aw[i]);
+      jmv(jt, E, t, av[i]);
+      cross_acc(vw, sw, aw[i]);
+      cross_acc(vw, sv, av[i]);
+      cross_acc(vv, sw, av[i]);
+      R In[3], If[3], hn[3], hf[3];
       inertia_mul(P, i, aw[i], av[i], In, If);
-      inertia_mul(P, i, pr.vw[i], pr.vv[i], pr.hn[i], pr.hf[i]);
-      for (int k = 0; k < 3; ++k) { pr.fn[i][k] = In[k]; pr.ff[i][k] = If[k]; }
-      cross_acc(pr.vw[i], pr.hn[i], pr.fn[i]);
-      cross_acc(pr.vv[i], pr.hf[i], pr.fn[i]);
-      cross_acc(pr.vw[i], pr.hf[i], pr.ff[i]);
+      inertia_mul(P, i, vw, vv, hn, hf);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { pr.hn[i][k] = hn[k]; pr.hf[i][k] = hf[k]; fn[i][k] = In[k]; ff[i][k] = If[k]; }
+      cross_acc(vw, hn, fn[i]);
+      cross_acc(vv, hf, fn[i]);
+      cross_acc(vw, hf, ff[i]);
       if (KIND == RK_QUAD) {
         if (pa < 0) {
+#pragma unroll
           for (int k = 0; k < 9; ++k) pr.E0[i][k] = E[k];
+#pragma unroll
           for (int k = 0; k < 3; ++k) pr.p0[i][k] = r[k];
         } else {
+#pragma unroll
           for (int a = 0; a < 3; ++a)
+#pragma unroll
             for (int b = 0; b < 3; ++b)
               pr.E0[i][a * 3 + b] = E[a * 3 + 0] * pr.E0[pa][b] + E[a * 3 + 1] * pr.E0[pa][3 + b] + E[a * 3 + 2] * pr.E0[pa][6 + b];
           R wr[3];
           mtv(pr.E0[pa], r, wr);
+#pragma unroll
           for (int k = 0; k < 3; ++k) pr.p0[i][k] = pr.p0[pa][k] + wr[k];
         }
       }
     }
     if (KIND == RK_QUAD) {
-      #pragma unroll
+#pragma unroll
       for (int ft = 0; ft < kFeet; ++ft) {
         const int bi = foot_body(ft);
         const R pt[3] = {P.foot_pt[ft][0], P.foot_pt[ft][1], P.foot_pt[ft][2]};
-        mtv(pr.E0[bi], pt, pr.wpt[ft]);
-        R wxp[3];
+        R wpt[3], vb[3], vwld[3], wxp[3];
+        mtv(pr.E0[bi], pt, wpt);
         cross(pr.vw[bi], pt, wxp);
-        for (int k = 0; k < 3; ++k) pr.vb[ft][k] = pr.vv[bi][k] + wxp[k];
-        mtv(pr.E0[bi], pr.vb[ft], pr.vwld[ft]);
-        const R bz = P.beta * (pr.p0[bi][2] + pr.wpt[ft][2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) vb[k] = pr.vv[bi][k] + wxp[k];
+        mtv(pr.E0[bi], vb, vwld);
+        const R bz = P.beta * (pr.p0[bi][2] + wpt[2]);
         R sp, gate;
         if (bz >= R(0)) {
           const R e = dexp(-bz);
@@ -800,29 +894,107 @@ struct SysRigid {
           sp = (R(1) / P.beta) * (dlog1p(e) - bz);
           gate = R(1) / (R(1) + e);
         }
+        R F[3];
+        F[0] = -(P.dc * (gate * vwld[0]));
+        F[1] = -(P.dc * (gate * vwld[1]));
+        F[2] = P.kc * sp - P.dc * (gate * vwld[2]);
         pr.gate[ft] = gate;
-        R* F = pr.F[ft];
-        F[0] = -(P.dc * (gate * pr.vwld[ft][0]));
-        F[1] = -(P.dc * (gate * pr.vwld[ft][1]));
-        F[2] = P.kc * sp - P.dc * (gate * pr.vwld[ft][2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { pr.wpt[ft][k] = wpt[k]; pr.vb[ft][k] = vb[k]; pr.vwld[ft][k] = vwld[k]; pr.F[ft][k] = F[k]; }
         R mw[3], mb[3], fb[3];
-        cross(pr.wpt[ft], F, mw);
+        cross(wpt, F, mw);
         mv(pr.E0[bi], mw, mb);
         mv(pr.E0[bi], F, fb);
-        for (int k = 0; k < 3; ++k) { pr.fn[bi][k] -= mb[k]; pr.ff[bi][k] -= fb[k]; }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { fn[bi][k] -= mb[k]; ff[bi][k] -= fb[k]; }
       }
     }
-    #pragma unroll
+#pragma unroll
     for (int i = N - 1; i >= 0; --i) {
       const int jt = jtype(i);
-      pr.tau[i] = jt <= 2 ? pr.fn[i][jt] : pr.ff[i][jt - 3];
+      h[i] = jt <= 2 ? fn[i][jt] : ff[i][jt - 3];
       const int pa = parent(i);
       if (pa >= 0) {
         R en[3], ef[3], rf[3];
-        jmtv(jt, pr.E[i], pr.fn[i], en);
-        jmtv(jt, pr.E[i], pr.ff[i], ef);
+        jmtv(jt, pr.E[i], fn[i], en);
+        jmtv(jt, pr.E[i], ff[i], ef);
         cross(pr.r[i], ef, rf);
-        for (int k = 0; k < 3; ++k) { pr.fn[pa][k] += en[k] + rf[k]; pr.ff[pa][k] += ef[k]; }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { fn[pa][k] += en[k] + rf[k]; ff[pa][k] += ef[k]; }
+      }
+    }
+  }
+
+  // accel_store (one lane, after the solve put qdd in pr): the accelerations
+  // with qdd, the parents' acceleration transforms, and the body forces as
+  // sent to the parent (children and contact included), from the stored
+  // transforms, velocities, I v and contact forces.
+  template <class R>
+  TO_DEV static void accel_store(const ParamsT<R>& P, Prim<R>& pr) {
+    R av[N][3], fn[N][3], ff[N][3];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int pa = parent(i), jt = jtype(i);
+      R paw[3], pav[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        paw[k] = pa < 0 ? R(0) : pr.aw[pa][k];
+        pav[k] = pa < 0 ? -P.g[k] : av[pa][k];
+      }
+      const R* E = pr.E[i];
+      R t[3], rw[3], Epa[3], Epb[3], vw[3], vv[3], hn[3], hf[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { vw[k] = pr.vw[i][k]; vv[k] = pr.vv[i][k]; hn[k] = pr.hn[i][k]; hf[k] = pr.hf[i][k]; }
+      cross(pr.r[i], paw, rw);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t[k] = pav[k] - rw[k];
+      jmv(jt, E, paw, Epa);
+      jmv(jt, E, t, Epb);
+      R sw[3] = {R(0), R(0), R(0)}, sv[3] = {R(0), R(0), R(0)};
+      if (jt <= 2) sw[jt] = pr.qd[i]; else sv[jt - 3] = pr.qd[i];
+      R aw[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { pr.Epa[i][k] = Epa[k]; pr.Epb[i][k] = Epb[k]; aw[k] = Epa[k]; av[i][k] = Epb[k]; }
+      cross_acc(vw, sw, aw);
+      cross_acc(vw, sv, av[i]);
+      cross_acc(vv, sw, av[i]);
+      if (jt <= 2) aw[jt] += pr.qdd[i]; else av[i][jt - 3] += pr.qdd[i];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pr.aw[i][k] = aw[k];
+      R In[3], If[3];
+      inertia_mul(P, i, aw, av[i], In, If);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { fn[i][k] = In[k]; ff[i][k] = If[k]; }
+      cross_acc(vw, hn, fn[i]);
+      cross_acc(vv, hf, fn[i]);
+      cross_acc(vw, hf, ff[i]);
+    }
+    if (KIND == RK_QUAD) {
+#pragma unroll
+      for (int ft = 0; ft < kFeet; ++ft) {
+        const int bi = foot_body(ft);
+        R mw[3], mb[3], fb[3];
+        cross(pr.wpt[ft], pr.F[ft], mw);
+        mv(pr.E0[bi], mw, mb);
+        mv(pr.E0[bi], pr.F[ft], fb);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { fn[bi][k] -= mb[k]; ff[bi][k] -= fb[k]; }
+      }
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+      const int jt = jtype(i);
+      pr.tau[i] = jt <= 2 ? fn[i][jt] : ff[i][jt - 3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { pr.fn[i][k] = fn[i][k]; pr.ff[i][k] = ff[i][k]; }
+      const int pa = parent(i);
+      if (pa >= 0) {
+        R en[3], ef[3], rf[3];
+        jmtv(jt, pr.E[i], fn[i], en);
+        jmtv(jt, pr.E[i], ff[i], ef);
+        cross(pr.r[i], ef, rf);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { fn[pa][k] += en[k] + rf[k]; ff[pa][k] += ef[k]; }
       }
     }
   }
@@ -836,7 +1008,7 @@ struct SysRigid {
   TO_DEV static void rnea_tangent(const ParamsT<R>& P, const Prim<R>& pr, const R* dq, const R* dqd, R* dtau) {
     R dvw[N][3], dvv[N][3], daw[N][3], dav[N][3], dfn[N][3], dff[N][3];
     R dE0[KIND == RK_QUAD ? N : 1][9], dp0[KIND == RK_QUAD ? N : 1][3];
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) {
       const int pa = parent(i);
       const int jt = jtype(i);
@@ -924,7 +1096,7 @@ struct SysRigid {
       }
     }
     if (KIND == RK_QUAD) {
-      #pragma unroll
+#pragma unroll
       for (int ft = 0; ft < kFeet; ++ft) {
         const int bi = foot_body(ft);
         const R pt[3] = {P.foot_pt[ft][0], P.foot_pt[ft][1], P.foot_pt[ft][2]};
@@ -957,7 +1129,7 @@ struct SysRigid {
         for (int k = 0; k < 3; ++k) { dfn[bi][k] -= dmb[k]; dff[bi][k] -= dfb[k]; }
       }
     }
-    #pragma unroll
+#pragma unroll
     for (int i = N - 1; i >= 0; --i) {
       const int jt = jtype(i);
       const bool rev = jt <= 2;
@@ -1004,28 +1176,38 @@ struct SysRigid {
     const int c = g.lane;
     const bool dir = c < n + m;
     R dq[N], dqd[N];
-    #pragma unroll
+#pragma unroll
     for (int i = 0; i < N; ++i) {
       dq[i] = (c == i) ? R(1) : R(0);
       dqd[i] = (c == N + i) ? R(1) : R(0);
     }
     if (c == 0)
-      #pragma unroll
+#pragma unroll
       for (int i = 0; i < N; ++i) { pr.q[i] = x[i]; pr.qd[i] = x[N + i]; pr.tin[i] = i < A0 ? R(0) : u[i - A0]; }
     const R h = P.dt / (R)P.n_sub;
+    // the mass matrix is formed on another warp, concurrently with the bias pass
+    constexpr int kMassLane = G > 32 ? 32 : 0;
     for (int s = 0; s < P.n_sub; ++s) {
+      g.sync();   // lane 0's substep state (initial, or just updated) before lane kMassLane reads q
+      R hb[N];
+      if (c == 0) bias_store(P, pr, hb);
+      if (c == kMassLane) mass_chol_mem(P, pr.q, pr.L);
+      g.sync();
       if (c == 0) {
-        accel(P, pr.q, pr.qd, pr.tin, pr.qdd, pr.L);
-        rnea_store(P, pr);
+        R rhs[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) rhs[i] = pr.tin[i] - hb[i];
+        chol_solve(P, pr.L, rhs, pr.qdd);
+        accel_store(P, pr);
       }
       g.sync();
       if (dir) {
         R dtau[N], rhs[N], dqdd[N];
         rnea_tangent(P, pr, dq, dqd, dtau);
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < N; ++i) rhs[i] = ((c >= n && i == A0 + (c - n)) ? R(1) : R(0)) - dtau[i];
         chol_solve(P, pr.L, rhs, dqdd);
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < N; ++i) {
           dqd[i] = dqd[i] + h * dqdd[i];
           dq[i] = dq[i] + h * dqd[i];
@@ -1033,7 +1215,7 @@ struct SysRigid {
       }
       g.sync();
       if (c == 0)
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < N; ++i) {
           pr.qd[i] = pr.qd[i] + h * pr.qdd[i];
           pr.q[i] = pr.q[i] + h * pr.qd[i];
@@ -1041,10 +1223,10 @@ struct SysRigid {
     }
     if (dir) {
       if (c < n) {
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < N; ++i) { A[i * n + c] = dq[i]; A[(N + i) * n + c] = dqd[i]; }
       } else {
-        #pragma unroll
+#pragma unroll
         for (int i = 0; i < N; ++i) { B[i * m + (c - n)] = dq[i]; B[(N + i) * m + (c - n)] = dqd[i]; }
       }
     }
