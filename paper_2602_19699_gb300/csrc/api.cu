@@ -227,6 +227,8 @@ int tocreate_problem(const to_problem_desc* d, to_problem* out) {
   p->sys = d->sys; p->n = d->n; p->m = d->m; p->T_max = d->T_max;
   p->ops = ops;
   p->params.assign(d->params, d->params + d->n_params);
+  if (ops->knot_scratch)
+    for (int pi = 0; pi < 2; ++pi) p->knot_scratch[pi] = ops->knot_scratch(d->params, d->n_params, pi);
   cudaGetDevice(&p->device);
   cudaError_t e = cudaMalloc(&p->d_params[0], blob64.size());
   if (e == cudaSuccess) e = cudaMemcpy(p->d_params[0], blob64.data(), blob64.size(), cudaMemcpyHostToDevice);
@@ -275,8 +277,8 @@ void todestroy_problem(to_problem p) {
 
 static void free_batch_buffers(to_batch b) {
   void* ptrs[] = {b->x0, b->T, b->U_init, b->forced, b->toff, b->order, b->hist, b->err, b->queue, b->traj,
-                  b->gains, b->vx, b->J, b->iters, b->status, b->slot, b->ahist, b->Jhist, b->gX, b->gU, b->gV, b->gK,
-                  b->prof};
+                  b->gains, b->dscr, b->vx, b->J, b->iters, b->status, b->slot, b->ahist, b->Jhist, b->gX, b->gU,
+                  b->gV, b->gK, b->prof};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -299,7 +301,7 @@ static cudaError_t grow(T*& ptr, size_t count, size_t& bytes) {
 static size_t workspace_bytes(const to_problem p, int B, long long knots, int elem, int prec_idx) {
   const SysOps* o = p->ops;
   size_t s = (size_t)B * (p->n * 8 + 4 + 8 + 4 + 8 + 4 + 4) + (size_t)(p->T_max + 2) * 4 + 8;
-  s += (size_t)knots * (kMaxSlots * o->rs[prec_idx] + o->gs[prec_idx]) * elem;
+  s += (size_t)knots * (kMaxSlots * o->rs[prec_idx] + o->gs[prec_idx] + p->knot_scratch[prec_idx]) * elem;
   return s;
 }
 
@@ -337,6 +339,10 @@ int tocreate_batch(to_problem p, int B_max, long long knots_max, const to_solver
     bytes += (size_t)knots_max * (kMaxSlots * o->rs[prec_idx] + o->gs[prec_idx]) * elem;
     e = cudaMalloc(&b->traj, (size_t)knots_max * kMaxSlots * o->rs[prec_idx] * elem);
     if (e == cudaSuccess) e = cudaMalloc(&b->gains, (size_t)knots_max * o->gs[prec_idx] * elem);
+  }
+  if (e == cudaSuccess && p->knot_scratch[prec_idx]) {
+    bytes += (size_t)knots_max * p->knot_scratch[prec_idx] * elem;
+    e = cudaMalloc(&b->dscr, (size_t)knots_max * p->knot_scratch[prec_idx] * elem);
   }
   b->bytes = bytes;
   if (e != cudaSuccess) {
@@ -453,6 +459,9 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   a.x0 = d_x0; a.T = d_T; a.U_init = d_U; a.forced = d_forced;
   a.toff = b->toff; a.order = b->order; a.queue = b->queue;
   a.traj = b->traj; a.gains = b->gains; a.vx = o->want_vx ? b->vx : nullptr;
+  a.kscr = (long long)p->knot_scratch[prec == PREC_FP64 ? 0 : 1];
+  a.dscr = b->dscr;
+  if (a.kscr && !a.dscr) return fail(TO_ERR_ARG, "solve: the batch has no derivative scratch for this precision");
   a.J_out = b->J; a.iters_out = b->iters; a.status_out = b->status; a.slot_out = b->slot;
   a.ahist = b->ahist; a.Jhist = b->Jhist;
   a.params = p->d_params[prec == PREC_FP64 ? 0 : 1]; a.actor_w = p->d_actor; a.err = b->err;
@@ -746,7 +755,8 @@ int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_
                o_slot = take(sizeof(int) * B), o_ahist = take(sizeof(int) * (size_t)B * mi),
                o_jhist = take(sizeof(double) * (size_t)B * (mi + 1)),
                o_traj = take((size_t)knots * kMaxSlots * ops->rs[pi] * elem),
-               o_gains = take((size_t)knots * ops->gs[pi] * elem);
+               o_gains = take((size_t)knots * ops->gs[pi] * elem),
+               o_dscr = take((size_t)knots * p->knot_scratch[pi] * elem);
   if (off > TO_NOALLOC_SCRATCH_BYTES)
     return fail(TO_ERR_BUDGET, "tosolve_batch_noalloc: needs " + std::to_string(off) + " bytes of workspace, more than "
                                    "the static " + std::to_string((size_t)TO_NOALLOC_SCRATCH_BYTES) + " bytes");
@@ -765,6 +775,7 @@ int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_
   w.Jhist = reinterpret_cast<double*>(base + o_jhist);
   w.traj = base + o_traj;
   w.gains = base + o_gains;
+  w.dscr = p->knot_scratch[pi] ? base + o_dscr : nullptr;
   w.J = d_J;
   w.iters = d_iters;
   w.status = d_status;

@@ -16,6 +16,7 @@ struct to_problem_s {
   void* d_params[2] = {nullptr, nullptr};   // parameter struct in float64, float32
   float* d_actor = nullptr;
   size_t n_actor = 0;
+  size_t knot_scratch[2] = {0, 0};   // per-knot derivative scratch elements (FP64, mixed); 0 = none
   int tuned_G[2] = {0, 0};     // autotuned launch shape per precision (FP64, mixed); 0 = none
   int tuned_gpb[2] = {0, 0};
 };
@@ -43,6 +44,7 @@ struct to_batch_s {
   // workspace
   void* traj = nullptr;
   void* gains = nullptr;
+  void* dscr = nullptr;      // per-knot derivative scratch (systems with knot_scratch)
   double* vx = nullptr;
   // results
   double* J = nullptr;

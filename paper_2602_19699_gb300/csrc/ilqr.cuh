@@ -87,6 +87,8 @@ struct SolveArgs {
   double* Jhist;            // B x (max_iter + 1)
   const void* params;       // the system's parameter struct in the kernel's precision
   const float* actor_w;     // actor weights or null
+  void* dscr;               // per-knot derivative scratch (stored substep primals) or null
+  long long kscr;           // its elements per knot
   const int* err;           // set by the prepare kernel on malformed input
   unsigned long long* prof; // 8 per-phase cycle counters, or null (tracing off)
 };
@@ -157,7 +159,7 @@ struct Work {
   R xl[n];               // low parts of x_k (float32 rollouts)
   R K[m * n];            // gains K_k, k_k (adjacent)
   R kf[m];
-  R sx[Sys::template Scratch<R>::elems];   // the system's derivative scratch (rigid trees: per-substep primal)
+  alignas(16) R sx[Sys::template Scratch<R>::elems];   // the system's derivative scratch (rigid trees: per-substep primal)
   int flag;              // Cholesky: 0 ok, 1 regularised, 2 failed
   int sel;
   int wslot;             // slot of the accepted line-search candidate
@@ -197,6 +199,7 @@ struct Solver {
     else return true;
   }
   static_assert(step_slots_fit<Sys>(), "line-search lanes exceed the system's step slots");
+  static_assert(!Sys::kKnotParallel || G > 32, "knot-parallel derivatives hold CTA-wide barriers");
   typedef typename Sys::template ParamsT<R> Params;
   static constexpr bool kLane = (G == 1);                  // one thread per instance, matrices in registers
   typedef std::conditional_t<kLane, WorkLane, Work<Sys, R>> W;
@@ -381,7 +384,7 @@ struct Solver {
   // ------------------------------------------------------------------------
   TO_DEV static int backward_knot(const Params& P, const Group<G>& g, W& w, bool act, bool act_next,
                                   const SolveArgs& a, R (&pb)[PB], const R* trec_next, R* grec, double* vxrec,
-                                  double mu_lm, bool timer, long long& tlast) {
+                                  double mu_lm, bool timer, long long& tlast, const R* kprim) {
     const R eps = (R)a.eps;
     if (act) {
 #pragma unroll
@@ -401,7 +404,12 @@ struct Solver {
     // dynamics Jacobians and clipped running-cost derivatives
     // (a system whose derivative step holds group barriers has groups of a
     // whole warp or CTA, so act is uniform over every barrier's scope)
-    if (act) Sys::template derivs<R, G>(P, g, w.xk, w.uk, eps, w.A, w.Bm, w.lxx, w.lx, w.luu, w.lu, w.sx);
+    if (act) {
+      if constexpr (Sys::kKnotParallel)
+        Sys::template derivs_staged<R, G>(P, g, w.xk, w.uk, eps, w.A, w.Bm, w.lxx, w.lx, w.luu, w.lu, w.sx, kprim);
+      else
+        Sys::template derivs<R, G>(P, g, w.xk, w.uk, eps, w.A, w.Bm, w.lxx, w.lx, w.luu, w.lu, w.sx);
+    }
     g.sync();
     TO_TICK(1);
     // V A and V B
@@ -891,6 +899,19 @@ struct Solver {
               if (e < n + m) pb[s] = r[e];
             }
           }
+          if constexpr (Sys::kKnotParallel) {
+            // every lane: the substep primal chains of its knots (group-uniform: one group per CTA)
+            if (bw)
+              for (int k = g.lane; k < T; k += G) {
+                const R* r = rec(traj, base, k, cur);
+                R x[n], u[m];
+#pragma unroll
+                for (int i = 0; i < n; ++i) x[i] = r[i];
+#pragma unroll
+                for (int i = 0; i < m; ++i) u[i] = r[n + i];
+                Sys::primal_knot(P, x, u, reinterpret_cast<R*>(a.dscr) + (base + k) * a.kscr);
+              }
+          }
           g.sync();
           TO_TICK(1);
           for (int k = kmax - 1; k >= 0; --k) {
@@ -898,8 +919,10 @@ struct Solver {
             const bool act_next = bw && k >= 1 && k - 1 < T;
             const long long kk = base + (act ? k : 0);
             const R* rn = rec(traj, base, act_next ? k - 1 : 0, cur);
+            const R* kprim = Sys::kKnotParallel ? reinterpret_cast<const R*>(a.dscr) + kk * a.kscr : nullptr;
             const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, gains + kk * GS,
-                                        (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, mu_lm, timer, tlast);
+                                        (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, mu_lm, timer, tlast,
+                                        kprim);
             if (f == 1) flags |= ST_FLAG_REG;
             // Levenberg-Marquardt: any failed factor (pivot test, or a
             // non-finite Q_uu once an earlier knot's gains were skipped)

@@ -35,6 +35,9 @@ struct SysOps {
   cudaError_t (*occupancy)(int prec, int G, int gpb, size_t* smem, int* blocks_per_sm);
   // per-knot costs of the final trajectories in float64 (critic targets)
   cudaError_t (*knot_costs)(const KnotCostArgs& a, cudaStream_t s);
+  // elements of per-knot derivative scratch (stored substep primals) for a
+  // parameter vector and precision (0 FP64, 1 mixed); null: none
+  size_t (*knot_scratch)(const double* p, size_t np, int prec);
 };
 
 const SysOps* sys_ops(int sys);

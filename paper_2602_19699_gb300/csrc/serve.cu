@@ -189,7 +189,7 @@ int toserver_create(const to_problem* problems, int n_problems, const to_solver_
     L.p = p;
     const int pr = s->opts.prec == TO_FP64 ? 0 : 1;
     const int elem = pr == 0 ? 8 : 4;
-    const size_t per_seat = (size_t)(p->T_max + 1) * (kMaxSlots * p->ops->rs[pr] + p->ops->gs[pr]) * elem +
+    const size_t per_seat = (size_t)(p->T_max + 1) * (kMaxSlots * p->ops->rs[pr] + p->ops->gs[pr] + p->knot_scratch[pr]) * elem +
                             (size_t)(s->opts.max_iter + 1) * 12 + 64;
     L.seats = (int)std::min<size_t>(budget / n_problems / per_seat, 1 << 16);
     if (L.seats < 1) {

@@ -1,4 +1,5 @@
 // Quadruped-shaped floating base: parameter parsing and solver instantiation.
+#include <algorithm>
 #include <cmath>
 
 #include "rigid_parse.cuh"
@@ -31,6 +32,12 @@ static int parse_quad(const double* p, size_t np, std::vector<unsigned char>& bl
 
 typedef Dispatch<SysQuad, 64> QDispatch;
 
+// the stored substep primals of one knot: n_sub of them (header [6], 0 means 1)
+static size_t quad_knot_scratch(const double* p, size_t np, int prec) {
+  const int n_sub = np > 6 ? std::max(1, (int)p[6]) : 1;
+  return (size_t)n_sub * (prec == 0 ? SysQuad::kPrimStride<double> : SysQuad::kPrimStride<float>);
+}
+
 static SysOps make_ops() {
   SysOps o{};
   o.sys = 4;
@@ -44,6 +51,7 @@ static SysOps make_ops() {
   o.launch = QDispatch::launch;
   o.occupancy = QDispatch::occupancy;
   o.knot_costs = knot_costs_one<SysQuad>;
+  o.knot_scratch = quad_knot_scratch;
   return o;
 }
 

@@ -30,6 +30,7 @@ struct SysDubins {
   template <class R> using ParamsT = DubinsParams<R>;
   template <class R> struct Scratch { static constexpr int elems = 1; };
   template <int G> static constexpr bool kGroupStep = false;
+  static constexpr bool kKnotParallel = false;
 
 
   template <class R>

@@ -46,6 +46,7 @@ struct SysPlanar3 {
   template <class R> using ParamsT = Planar3Params<R>;
   template <class R> struct Scratch { static constexpr int elems = 1; };
   template <int G> static constexpr bool kGroupStep = false;
+  static constexpr bool kKnotParallel = false;
 
   // absolute link angles, link and centre-of-mass vectors, joint positions
   template <class R>

@@ -26,6 +26,7 @@ struct SysPointMass {
   template <class R> using ParamsT = PointMassParams<R>;
   template <class R> struct Scratch { static constexpr int elems = 1; };
   template <int G> static constexpr bool kGroupStep = false;
+  static constexpr bool kKnotParallel = false;
 
 
   template <class R>

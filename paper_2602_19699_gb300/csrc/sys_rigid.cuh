@@ -760,6 +760,16 @@ struct SysRigid {
     R E0[KIND == RK_QUAD ? N : 1][9], p0[KIND == RK_QUAD ? N : 1][3];
     R wpt[NF][3], F[NF][3], vb[NF][3], vwld[NF][3], gate[NF];
   };
+  // Knot-parallel derivatives (quadruped): before each backward pass every
+  // lane runs the substep primal chains of its own knots (primal_knot) and
+  // stores each substep's Prim in a per-knot global scratch; inside the
+  // backward pass the group stages those Prims into shared memory
+  // (cp.async, one substep ahead) and every direction lane runs its tangent
+  // pass at once (derivs_staged).  No lane waits for a primal.
+  static constexpr bool kKnotParallel = (KIND == RK_QUAD);
+  // elements per stored substep primal (a whole number of 16-byte chunks)
+  template <class R> static constexpr int kPrimStride = (int)(((sizeof(Prim<R>) + 15) / 16 * 16) / sizeof(R));
+
   // Line search of a 64-lane group: candidate lane c < kStepSlots steps its
   // rollout with lane c + 32 (the other warp) as its partner, which forms and
   // factors the mass matrix while lane c runs the bias Newton-Euler pass.
@@ -770,7 +780,7 @@ struct SysRigid {
   // area): the derivative primal, or the line search's per-candidate slots
   template <class R>
   struct Scratch {
-    static constexpr int prim = (int)((sizeof(Prim<R>) + sizeof(R) - 1) / sizeof(R));
+    static constexpr int prim = (KIND == RK_QUAD ? 2 : 1) * kPrimStride<R>;   // double buffer when staged
     static constexpr int step = KIND == RK_QUAD ? kStepSlots * kStepSlot + kStepSlots : 0;
     static constexpr int elems = prim > step ? prim : step;
   };
@@ -801,13 +811,13 @@ struct SysRigid {
   // bias_store (one lane): those quantities, I v, and the inverse dynamics at
   // qdd = 0 (gravity, velocity products, contact), i.e. the bias torques h.
   template <class R>
-  TO_DEV static void bias_store(const ParamsT<R>& P, Prim<R>& pr, R* h) {
+  TO_DEV static void bias_store(const ParamsT<R>& P, Prim<R>& pr, const R* q, const R* qd, R* h) {
     R aw[N][3], av[N][3], fn[N][3], ff[N][3];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const int pa = parent(i), jt = jtype(i);
       R E[9], r[3];
-      joint_transform(P, i, pr.q[i], E, r);
+      joint_transform(P, i, q[i], E, r);
 #pragma unroll
       for (int k = 0; k < 9; ++k) pr.E[i][k] = E[k];
 #pragma unroll
@@ -827,7 +837,7 @@ struct SysRigid {
       jmv(jt, E, pw, Epw);
       jmv(jt, E, t, Ept);
       R sw[3] = {R(0), R(0), R(0)}, sv[3] = {R(0), R(0), R(0)};
-      if (jt <= 2) sw[jt] = pr.qd[i]; else sv[jt - 3] = pr.qd[i];
+      if (jt <= 2) sw[jt] = qd[i]; else sv[jt - 3] = qd[i];
       R vw[3], vv[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -1159,6 +1169,101 @@ struct SysRigid {
     }
   }
 
+  // The substep primal chain of one knot on one lane, every substep's Prim
+  // stored at out + s kPrimStride (global memory): the same arithmetic as
+  // derivs' primal lane, with the mass matrix factored on this lane.
+  template <class R>
+  TO_DEV static void primal_knot(const ParamsT<R>& P, const R* x, const R* u, R* out) {
+    R q[N], qd[N], tin[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) { q[i] = x[i]; qd[i] = x[N + i]; tin[i] = i < A0 ? R(0) : u[i - A0]; }
+    const R h = P.dt / (R)P.n_sub;
+    for (int s = 0; s < P.n_sub; ++s) {
+      Prim<R>& pr = *reinterpret_cast<Prim<R>*>(out + (size_t)s * kPrimStride<R>);
+      R hb[N], L[N * N], rhs[N], qdd[N];
+      bias_store(P, pr, q, qd, hb);
+      mass_chol(P, q, L);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        pr.L[k * N + k] = L[k * N + k];
+#pragma unroll
+        for (int d = 1; d <= kDepthMax; ++d)
+          if (d <= depth(k)) pr.L[k * N + anc(k, d)] = L[k * N + anc(k, d)];
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) rhs[i] = tin[i] - hb[i];
+      chol_solve(P, L, rhs, qdd);
+#pragma unroll
+      for (int i = 0; i < N; ++i) { pr.q[i] = q[i]; pr.qd[i] = qd[i]; pr.tin[i] = tin[i]; pr.qdd[i] = qdd[i]; }
+      accel_store(P, pr);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        qd[i] = qd[i] + h * qdd[i];
+        q[i] = q[i] + h * qd[i];
+      }
+    }
+  }
+
+  // group copy of one stored Prim into shared memory, 16 bytes per cp.async
+  template <class R, int G>
+  TO_DEV static void stage_prim(const Group<G>& g, const R* src, R* dst) {
+    constexpr int chunks = kPrimStride<R> * (int)sizeof(R) / 16;
+    const char* s = reinterpret_cast<const char*>(src);
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    for (int c = g.lane; c < chunks; c += G)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * c), "l"(s + 16 * c) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+
+  // Columns of [A | B] from the knot's stored substep primals (prims, global):
+  // each substep's Prim is staged into shared memory one substep ahead while
+  // the direction lanes run the tangent pass of the current one.
+  template <class R, int G>
+  TO_DEV static void derivs_staged(const ParamsT<R>& P, const Group<G>& g, const R* x, const R* u, R eps, R* A, R* B,
+                                   R* lxx, R* lx, R* luu, R* lu, R* scratch, const R* prims) {
+    static_assert(G >= n + m, "one lane per tangent direction");
+    const int c = g.lane;
+    const bool dir = c < n + m;
+    R dq[N], dqd[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      dq[i] = (c == i) ? R(1) : R(0);
+      dqd[i] = (c == N + i) ? R(1) : R(0);
+    }
+    const R h = P.dt / (R)P.n_sub;
+    stage_prim<R, G>(g, prims, scratch);
+    for (int s = 0; s < P.n_sub; ++s) {
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      g.sync();   // substep s staged by every lane; every lane done with the other buffer
+      if (s + 1 < P.n_sub)
+        stage_prim<R, G>(g, prims + (size_t)(s + 1) * kPrimStride<R>, scratch + ((s + 1) & 1) * kPrimStride<R>);
+      const Prim<R>& pr = *reinterpret_cast<const Prim<R>*>(scratch + (s & 1) * kPrimStride<R>);
+      if (dir) {
+        R dtau[N], rhs[N], dqdd[N];
+        rnea_tangent(P, pr, dq, dqd, dtau);
+#pragma unroll
+        for (int i = 0; i < N; ++i) rhs[i] = ((c >= n && i == A0 + (c - n)) ? R(1) : R(0)) - dtau[i];
+        chol_solve(P, pr.L, rhs, dqdd);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          dqd[i] = dqd[i] + h * dqdd[i];
+          dq[i] = dq[i] + h * dqd[i];
+        }
+      }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (dir) {
+      if (c < n) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) { A[i * n + c] = dq[i]; A[(N + i) * n + c] = dqd[i]; }
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) { B[i * m + (c - n)] = dq[i]; B[(N + i) * m + (c - n)] = dqd[i]; }
+      }
+    }
+    if (c == G - 1) running_derivs(P, x, u, eps, lxx, lx, luu, lu);
+  }
+
   // Columns of [A | B]: lane c < n carries the tangent e_c of the state,
   // lane n + j the tangent of control j, through the n_sub substeps.  Per
   // substep, lane 0 evaluates the primal once (acceleration by the
@@ -1190,7 +1295,7 @@ struct SysRigid {
     for (int s = 0; s < P.n_sub; ++s) {
       g.sync();   // lane 0's substep state (initial, or just updated) before lane kMassLane reads q
       R hb[N];
-      if (c == 0) bias_store(P, pr, hb);
+      if (c == 0) bias_store(P, pr, pr.q, pr.qd, hb);
       if (c == kMassLane) mass_chol_mem(P, pr.q, pr.L);
       g.sync();
       if (c == 0) {
