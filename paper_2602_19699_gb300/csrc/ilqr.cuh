@@ -199,7 +199,7 @@ struct Solver {
     else return true;
   }
   static_assert(step_slots_fit<Sys>(), "line-search lanes exceed the system's step slots");
-  static_assert(!Sys::kKnotParallel || G > 32, "knot-parallel derivatives hold CTA-wide barriers");
+  static_assert(!Sys::kKnotParallel || G >= 32, "knot-parallel derivatives need groups of whole warps");
   typedef typename Sys::template ParamsT<R> Params;
   static constexpr bool kLane = (G == 1);                  // one thread per instance, matrices in registers
   typedef std::conditional_t<kLane, WorkLane, Work<Sys, R>> W;
@@ -900,7 +900,7 @@ struct Solver {
             }
           }
           if constexpr (Sys::kKnotParallel) {
-            // every lane: the substep primal chains of its knots (group-uniform: one group per CTA)
+            // every lane: the substep primal chains of its knots (bw is uniform over a group of whole warps)
             if (bw)
               for (int k = g.lane; k < T; k += G) {
                 const R* r = rec(traj, base, k, cur);

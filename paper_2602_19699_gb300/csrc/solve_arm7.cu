@@ -1,4 +1,5 @@
 // 7-DoF serial arm: parameter parsing and solver instantiation.
+#include <algorithm>
 #include <cmath>
 
 #include "rigid_parse.cuh"
@@ -26,6 +27,12 @@ static int parse_arm7(const double* p, size_t np, std::vector<unsigned char>& bl
 
 typedef Dispatch<SysArm7, 32> A7Dispatch;
 
+// the stored substep primals of one knot: n_sub of them (header [6], 0 means 1)
+static size_t arm7_knot_scratch(const double* p, size_t np, int prec) {
+  const int n_sub = np > 6 ? std::max(1, (int)p[6]) : 1;
+  return (size_t)n_sub * (prec == 0 ? SysArm7::kPrimStride<double> : SysArm7::kPrimStride<float>);
+}
+
 static SysOps make_ops() {
   SysOps o{};
   o.sys = 3;
@@ -39,6 +46,7 @@ static SysOps make_ops() {
   o.launch = A7Dispatch::launch;
   o.occupancy = A7Dispatch::occupancy;
   o.knot_costs = knot_costs_one<SysArm7>;
+  o.knot_scratch = arm7_knot_scratch;
   return o;
 }
 

@@ -760,13 +760,13 @@ struct SysRigid {
     R E0[KIND == RK_QUAD ? N : 1][9], p0[KIND == RK_QUAD ? N : 1][3];
     R wpt[NF][3], F[NF][3], vb[NF][3], vwld[NF][3], gate[NF];
   };
-  // Knot-parallel derivatives (quadruped): before each backward pass every
+  // Knot-parallel derivatives (both trees): before each backward pass every
   // lane runs the substep primal chains of its own knots (primal_knot) and
   // stores each substep's Prim in a per-knot global scratch; inside the
   // backward pass the group stages those Prims into shared memory
   // (cp.async, one substep ahead) and every direction lane runs its tangent
   // pass at once (derivs_staged).  No lane waits for a primal.
-  static constexpr bool kKnotParallel = (KIND == RK_QUAD);
+  static constexpr bool kKnotParallel = true;
   // elements per stored substep primal (a whole number of 16-byte chunks)
   template <class R> static constexpr int kPrimStride = (int)(((sizeof(Prim<R>) + 15) / 16 * 16) / sizeof(R));
 
@@ -780,7 +780,7 @@ struct SysRigid {
   // area): the derivative primal, or the line search's per-candidate slots
   template <class R>
   struct Scratch {
-    static constexpr int prim = (KIND == RK_QUAD ? 2 : 1) * kPrimStride<R>;   // double buffer when staged
+    static constexpr int prim = 2 * kPrimStride<R>;   // the staged substep primals, double-buffered
     static constexpr int step = KIND == RK_QUAD ? kStepSlots * kStepSlot + kStepSlots : 0;
     static constexpr int elems = prim > step ? prim : step;
   };
