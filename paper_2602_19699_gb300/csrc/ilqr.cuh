@@ -165,6 +165,17 @@ struct Work {
   int wslot;             // slot of the accepted line-search candidate
 };
 
+// Element loop of a group whose loads should be in flight together: the
+// trips unroll (predicated), element e = lane + s G.
+template <int NE, int G, class F>
+TO_DEV void for_each_lane(const Group<G>& g, F&& f) {
+#pragma unroll
+  for (int s = 0; s < (NE + G - 1) / G; ++s) {
+    const int e = g.lane + s * G;
+    if (e < NE) f(e);
+  }
+}
+
 // per-lane workspace of single-lane groups: every matrix lives in registers
 struct WorkLane {
   double red;
@@ -404,7 +415,20 @@ struct Solver {
     // dynamics Jacobians and clipped running-cost derivatives
     // (a system whose derivative step holds group barriers has groups of a
     // whole warp or CTA, so act is uniform over every barrier's scope)
-    if (act) {
+    if constexpr (Sys::kStoredDerivs) {
+      // the knot's stored block: A, B, l_xx, l_x, l_uu, l_u
+      constexpr int DS = Sys::kDerivStride;
+      if (act)
+        for_each_lane<DS>(g, [&](int e) {
+          const R v = kprim[e];
+          if (e < n * n) w.A[e] = v;
+          else if (e < n * n + n * m) w.Bm[e - n * n] = v;
+          else if (e < 2 * n * n + n * m) w.lxx[e - n * n - n * m] = v;
+          else if (e < 2 * n * n + n * m + n) w.lx[e - 2 * n * n - n * m] = v;
+          else if (e < 2 * n * n + n * m + n + m * m) w.luu[e - 2 * n * n - n * m - n] = v;
+          else w.lu[e - 2 * n * n - n * m - n - m * m] = v;
+        });
+    } else if (act) {
       if constexpr (Sys::kKnotParallel)
         Sys::template derivs_staged<R, G>(P, g, w.xk, w.uk, eps, w.A, w.Bm, w.lxx, w.lx, w.luu, w.lu, w.sx, kprim);
       else
@@ -899,6 +923,25 @@ struct Solver {
               if (e < n + m) pb[s] = r[e];
             }
           }
+          if constexpr (Sys::kStoredDerivs) {
+            // every lane: the whole derivative block of its knots, stored
+            // (no barrier inside: the groups of a warp may run different T)
+            if (bw) {
+              const R eps = (R)a.eps;
+              for (int k = g.lane; k < T; k += G) {
+                const R* r = rec(traj, base, k, cur);
+                R x[n], u[m];
+#pragma unroll
+                for (int i = 0; i < n; ++i) x[i] = r[i];
+#pragma unroll
+                for (int i = 0; i < m; ++i) u[i] = r[n + i];
+                R d[Sys::kDerivStride];
+                Sys::derivs_lane(P, x, u, eps, d, d + n * n, d + n * n + n * m, d + 2 * n * n + n * m,
+                                 d + 2 * n * n + n * m + n, d + 2 * n * n + n * m + n + m * m);
+                st_vec<Sys::kDerivStride>(reinterpret_cast<R*>(a.dscr) + (base + k) * a.kscr, d);
+              }
+            }
+          }
           if constexpr (Sys::kKnotParallel) {
             // every lane: the substep primal chains of its knots (bw is uniform over a group of whole warps)
             if (bw)
@@ -919,7 +962,8 @@ struct Solver {
             const bool act_next = bw && k >= 1 && k - 1 < T;
             const long long kk = base + (act ? k : 0);
             const R* rn = rec(traj, base, act_next ? k - 1 : 0, cur);
-            const R* kprim = Sys::kKnotParallel ? reinterpret_cast<const R*>(a.dscr) + kk * a.kscr : nullptr;
+            const R* kprim = (Sys::kKnotParallel || Sys::kStoredDerivs) ? reinterpret_cast<const R*>(a.dscr) + kk * a.kscr
+                                                                          : nullptr;
             const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, gains + kk * GS,
                                         (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, mu_lm, timer, tlast,
                                         kprim);

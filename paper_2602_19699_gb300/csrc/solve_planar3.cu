@@ -44,6 +44,9 @@ static int parse_planar3(const double* p, size_t np, std::vector<unsigned char>&
 
 typedef Dispatch<SysPlanar3, 1, 8, 16, 32> P3Dispatch;
 
+// every knot's stored derivative block (both precisions)
+static size_t planar3_knot_scratch(const double*, size_t, int) { return SysPlanar3::kDerivStride; }
+
 static SysOps make_ops() {
   SysOps o{};
   o.sys = 2;
@@ -57,6 +60,7 @@ static SysOps make_ops() {
   o.launch = P3Dispatch::launch;
   o.occupancy = P3Dispatch::occupancy;
   o.knot_costs = knot_costs_one<SysPlanar3>;
+  o.knot_scratch = planar3_knot_scratch;
   return o;
 }
 

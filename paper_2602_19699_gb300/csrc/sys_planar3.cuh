@@ -47,6 +47,10 @@ struct SysPlanar3 {
   template <class R> struct Scratch { static constexpr int elems = 1; };
   template <int G> static constexpr bool kGroupStep = false;
   static constexpr bool kKnotParallel = false;
+  // derivatives computed for every knot before the backward pass, one knot
+  // per lane (derivs_lane), and stored: A, B, l_xx, l_x, l_uu, l_u
+  static constexpr bool kStoredDerivs = true;
+  static constexpr int kDerivStride = n * n + n * m + n * n + n + m * m + m;
 
   // absolute link angles, link and centre-of-mass vectors, joint positions
   template <class R>

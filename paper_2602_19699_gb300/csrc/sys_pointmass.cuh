@@ -27,6 +27,7 @@ struct SysPointMass {
   template <class R> struct Scratch { static constexpr int elems = 1; };
   template <int G> static constexpr bool kGroupStep = false;
   static constexpr bool kKnotParallel = false;
+  static constexpr bool kStoredDerivs = false;
 
 
   template <class R>

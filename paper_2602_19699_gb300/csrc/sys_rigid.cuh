@@ -767,6 +767,7 @@ struct SysRigid {
   // (cp.async, one substep ahead) and every direction lane runs its tangent
   // pass at once (derivs_staged).  No lane waits for a primal.
   static constexpr bool kKnotParallel = true;
+  static constexpr bool kStoredDerivs = false;
   // elements per stored substep primal (a whole number of 16-byte chunks)
   template <class R> static constexpr int kPrimStride = (int)(((sizeof(Prim<R>) + 15) / 16 * 16) / sizeof(R));
 
