@@ -25,7 +25,7 @@ struct SysOps {
   int sys, n, m;
   int rs[2], gs[2];                 // knot / gain record lengths (elements) for FP64, mixed
   int n_groups;                     // supported group sizes
-  int groups[4];
+  int groups[6];
   int default_G, default_gpb[2];    // default launch shape (FP64, mixed)
   bool accepts_actor;
   // parse the flat parameter vector into the system's struct in float64 and float32

@@ -42,7 +42,7 @@ static int parse_planar3(const double* p, size_t np, std::vector<unsigned char>&
   return 0;
 }
 
-typedef Dispatch<SysPlanar3, 1, 8, 16, 32> P3Dispatch;
+typedef Dispatch<SysPlanar3, 1, 4, 8, 16, 32> P3Dispatch;
 
 // every knot's stored derivative block (both precisions)
 static size_t planar3_knot_scratch(const double*, size_t, int) { return SysPlanar3::kDerivStride; }
@@ -51,8 +51,9 @@ static SysOps make_ops() {
   SysOps o{};
   o.sys = 2;
   fill_layout<SysPlanar3>(o);
-  o.n_groups = 4;
+  o.n_groups = 5;
   o.groups[0] = 8; o.groups[1] = 16; o.groups[2] = 32; o.groups[3] = 1;   // 1: one thread per instance
+  o.groups[4] = 4;   // stored derivatives need no lane per derivative role
   o.default_G = 8;
   o.default_gpb[0] = 8; o.default_gpb[1] = 8;
   o.accepts_actor = false;

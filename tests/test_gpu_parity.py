@@ -183,6 +183,22 @@ def test_planar3_replay_ragged(P, oracle_mod, prec, T, iters):
     _check_consistency(o, b, rg, prec, min_checked=b.x0.shape[0] // 4)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_planar3_replay_four_lanes(P, oracle_mod, prec):
+    # groups of 4 lanes (8 instances per warp): the stored derivative blocks
+    # make them possible for the planar arm
+    prob = W.planar3(seed=1)
+    b = W.make_batch(prob, 24, seed=2, T=(20, 120))
+    o = oracle_mod.Oracle.from_problem(prob)
+    ro = o.solve(b.x0, b.T, max_iter=20, tol=1e-8)
+    kappa = _sensitivity(o, b, ro, 20)
+    rg = _replay(P, prob, b, ro, P.TO_FP64 if prec == "fp64" else P.TO_MIXED, 20, T_max=128,
+                 group_lanes=4, groups_per_block=16)
+    well = _check(ro, rg, kappa, prec, b.T)
+    assert well.mean() >= (0.4 if prec == "fp64" else 0.2)
+    _check_consistency(o, b, rg, prec, min_checked=b.x0.shape[0] // 4)
+
+
 def test_pointmass_unforced_matches_oracle_choices(P, oracle_mod):
     prob = W.pointmass(seed=3)
     b = W.make_batch(prob, 64, seed=4)
