@@ -397,19 +397,21 @@ struct Solver {
                                   const SolveArgs& a, R (&pb)[PB], const R* trec_next, R* grec, double* vxrec,
                                   double mu_lm, bool timer, long long& tlast, const R* kprim) {
     const R eps = (R)a.eps;
-    if (act) {
+    if constexpr (!Sys::kStoredDerivs) {   // x_k, u_k feed the derivative step (stored blocks need neither)
+      if (act) {
 #pragma unroll
-      for (int s = 0; s < PB; ++s) {
-        const int e = g.lane + s * G;
-        if (e < n + m) w.xk[e] = pb[s];
+        for (int s = 0; s < PB; ++s) {
+          const int e = g.lane + s * G;
+          if (e < n + m) w.xk[e] = pb[s];
+        }
       }
-    }
-    g.sync();
-    if (act_next) {
+      g.sync();
+      if (act_next) {
 #pragma unroll
-      for (int s = 0; s < PB; ++s) {
-        const int e = g.lane + s * G;
-        if (e < n + m) pb[s] = trec_next[e];
+        for (int s = 0; s < PB; ++s) {
+          const int e = g.lane + s * G;
+          if (e < n + m) pb[s] = trec_next[e];
+        }
       }
     }
     // dynamics Jacobians and clipped running-cost derivatives

@@ -89,3 +89,27 @@ def test_noalloc_rejects_requests_beyond_the_static_workspace(P):
         P.tosolve_batch_noalloc(problem, B, z.data_ptr(), zi.data_ptr(), z.data_ptr(), zi.data_ptr(), zi.data_ptr())
     assert e.value.code == P.TO_ERR_BUDGET
     assert "static" in str(e.value)
+
+
+@pytest.mark.parametrize("sysname", ["arm7", "quad"])
+def test_noalloc_rigid_trees(P, sysname):
+    # the rigid trees' per-knot scratch (stored substep primals) comes out of
+    # the static array too
+    import torch
+    prob = W.arm7(seed=1) if sysname == "arm7" else W.quad(seed=2, with_actor=False)
+    T_max = 30 if sysname == "arm7" else 10
+    problem = P.tocreate_problem(prob.sys, prob.params, T_max)
+    opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=3)
+    b = W.make_batch(prob, 8, seed=3, T=(5, T_max))
+    x0 = torch.tensor(b.x0, dtype=torch.float64, device="cuda")
+    T = torch.tensor(b.T, dtype=torch.int32, device="cuda")
+    ref = _regular(P, problem, x0, T, opts)
+    got = _noalloc(P, problem, x0, T, opts)
+    np.testing.assert_array_equal(got["iters"], ref["iters"])
+    np.testing.assert_array_equal(got["status"], ref["status"])
+    ok = np.isfinite(ref["J"])
+    assert ok.sum() >= 4
+    assert np.all(np.abs(got["J"][ok] - ref["J"][ok]) <= MIXED_J_TOL * np.abs(ref["J"][ok]))
+    for key in ("X", "U"):
+        a, r = got[key][ok], ref[key][ok]
+        assert np.all(np.abs(a - r) <= MIXED_X_TOL * np.maximum(np.abs(r).max(axis=(1, 2), keepdims=True), 1e-300))
