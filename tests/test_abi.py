@@ -66,3 +66,26 @@ def test_product_path_does_not_touch_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle.cpp" not in text and "liboracle" not in text, f
+
+
+@pytest.mark.parametrize("case", ["quad_parent", "quad_axis", "arm7_axis", "quad_foot"])
+def test_parser_rejects_other_joint_trees(libto, case):
+    # the device model is compiled for one tree per system; anything else is
+    # refused by tocreate_problem's parser, before any CUDA call (no GPU needed)
+    from paper_2602_19699_gb300 import workload as W
+    P = libto
+    prob = W.quad(seed=0, with_actor=False) if case.startswith("quad") else W.arm7(seed=0)
+    p = prob.params.copy()
+    body = lambda i: W.RIGID_HEADER + W.BODY_STRIDE * i
+    if case == "quad_parent":
+        p[body(9)] = 8              # hip of leg 1 hung from leg 0's calf
+    elif case == "quad_axis":
+        p[body(7) + 1] = 0          # thigh about x instead of y
+    elif case == "arm7_axis":
+        p[body(3) + 1] = 2          # joint 3 about z instead of y
+    else:
+        c = W.rigid_cost_offset(18)
+        p[c + 11] = 7               # foot 0 on the thigh
+    with pytest.raises(P.ToError) as e:
+        P.tocreate_problem(prob.sys, p, 20)
+    assert e.value.code == P.TO_ERR_ARG

@@ -99,3 +99,4 @@ def test_quad_actor_warm_start(P, oracle_mod, prec):
     kappa = _sensitivity(o, b, ro, 2)
     rg = s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=2)
     _check(ro, rg, kappa, prec, b.T)
+
