@@ -13,10 +13,12 @@
 // coordinate, or a control) through the substeps:
 //   dqdd = M^{-1} (dtau - d ID(q, qd, qdd) / d(q, qd) . (dq, dqd)),
 // with the directional derivative of the inverse dynamics (qdd held fixed)
-// from a hand-written tangent pass over per-body primal quantities that one
-// lane stores in shared memory per substep (the product rule of the
-// Newton-Euler recursion; a dual-number pass of the same code serves the
-// arm's nested terminal Hessian).
+// from a hand-written tangent pass over per-body primal quantities (the
+// product rule of the Newton-Euler recursion).  The primal quantities of
+// every knot's substeps are computed before the backward pass, one knot per
+// lane, and stored; the tangent lanes stage them into shared memory.  A
+// dual-number pass of the same recursion serves the arm's nested terminal
+// Hessian.
 #pragma once
 #include "common.cuh"
 
@@ -1265,79 +1267,6 @@ struct SysRigid {
     if (c == G - 1) running_derivs(P, x, u, eps, lxx, lx, luu, lu);
   }
 
-  // Columns of [A | B]: lane c < n carries the tangent e_c of the state,
-  // lane n + j the tangent of control j, through the n_sub substeps.  Per
-  // substep, lane 0 evaluates the primal once (acceleration by the
-  // composite-rigid-body mass matrix, then the Newton-Euler quantities at
-  // that acceleration) into the group's shared scratch; every direction lane
-  // then runs only the tangent pass against it:
-  //   dqdd = M^{-1} (dtau - dID(q, qd, qdd)[dq, dqd]),
-  // and integrates its tangent like the state.  The last lane also writes
-  // the (separable) running-cost derivatives.
-  template <class R, int G>
-  TO_DEV static void derivs(const ParamsT<R>& P, const Group<G>& g, const R* x, const R* u, R eps, R* A, R* B,
-                            R* lxx, R* lx, R* luu, R* lu, R* scratch) {
-    static_assert(G >= n + m, "one lane per tangent direction");
-    Prim<R>& pr = *reinterpret_cast<Prim<R>*>(scratch);
-    const int c = g.lane;
-    const bool dir = c < n + m;
-    R dq[N], dqd[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      dq[i] = (c == i) ? R(1) : R(0);
-      dqd[i] = (c == N + i) ? R(1) : R(0);
-    }
-    if (c == 0)
-#pragma unroll
-      for (int i = 0; i < N; ++i) { pr.q[i] = x[i]; pr.qd[i] = x[N + i]; pr.tin[i] = i < A0 ? R(0) : u[i - A0]; }
-    const R h = P.dt / (R)P.n_sub;
-    // the mass matrix is formed on another warp, concurrently with the bias pass
-    constexpr int kMassLane = G > 32 ? 32 : 0;
-    for (int s = 0; s < P.n_sub; ++s) {
-      g.sync();   // lane 0's substep state (initial, or just updated) before lane kMassLane reads q
-      R hb[N];
-      if (c == 0) bias_store(P, pr, pr.q, pr.qd, hb);
-      if (c == kMassLane) mass_chol_mem(P, pr.q, pr.L);
-      g.sync();
-      if (c == 0) {
-        R rhs[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) rhs[i] = pr.tin[i] - hb[i];
-        chol_solve(P, pr.L, rhs, pr.qdd);
-        accel_store(P, pr);
-      }
-      g.sync();
-      if (dir) {
-        R dtau[N], rhs[N], dqdd[N];
-        rnea_tangent(P, pr, dq, dqd, dtau);
-#pragma unroll
-        for (int i = 0; i < N; ++i) rhs[i] = ((c >= n && i == A0 + (c - n)) ? R(1) : R(0)) - dtau[i];
-        chol_solve(P, pr.L, rhs, dqdd);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          dqd[i] = dqd[i] + h * dqdd[i];
-          dq[i] = dq[i] + h * dqd[i];
-        }
-      }
-      g.sync();
-      if (c == 0)
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          pr.qd[i] = pr.qd[i] + h * pr.qdd[i];
-          pr.q[i] = pr.q[i] + h * pr.qd[i];
-        }
-    }
-    if (dir) {
-      if (c < n) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) { A[i * n + c] = dq[i]; A[(N + i) * n + c] = dqd[i]; }
-      } else {
-#pragma unroll
-        for (int i = 0; i < N; ++i) { B[i * m + (c - n)] = dq[i]; B[(N + i) * m + (c - n)] = dqd[i]; }
-      }
-    }
-    if (c == G - 1) running_derivs(P, x, u, eps, lxx, lx, luu, lu);
-  }
 };
 
 typedef SysRigid<7, 0, RK_ARM7> SysArm7;
