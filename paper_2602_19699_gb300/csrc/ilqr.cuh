@@ -18,12 +18,17 @@
 // uneven horizons and iteration counts share one launch.  Groups that share a
 // warp run warp-uniform control flow; per-group work is predicated.  Every
 // phase prefetches the next knot record into registers while the current
-// knot computes.
+// knot computes.  Systems may move derivative work off the backward
+// recursion: the planar arm stores every knot's derivative block, the rigid
+// trees every knot's substep primals, computed before the pass one knot per
+// lane (per-knot scratch, a.dscr).  G = 1 (single-lane groups) keeps the
+// whole backward knot in registers (backward_lane).
 //
 // Arithmetic: R = double (FP64 mode) or float (mixed mode).  In mixed mode
 // rollouts, derivatives and Riccati products are float32; the Q_uu Cholesky
-// and its pivot test and the residual of the one-step refinement of the gain
-// solve are float64; the cost is accumulated as a compensated float32 pair
+// and its pivot test are float64; the residual of the one-step refinement of
+// the gain solve is float-float (refine = 1, about 48 significant bits) or
+// float64 (refine = 2); the cost is accumulated as a compensated float32 pair
 // (about 48 significant bits) and compared in float64.
 #pragma once
 #include <type_traits>
@@ -523,69 +528,69 @@ struct Solver {
       }
       g.sync();
     } else {
-    // V A and V B
-    if (act)
-      for (int e = g.lane; e < n * n + n * m; e += G) {
-        if (e < n * n) {
-          const int i = e / n, j = e % n;
-          R s = 0;
+      // V A and V B
+      if (act)
+        for (int e = g.lane; e < n * n + n * m; e += G) {
+          if (e < n * n) {
+            const int i = e / n, j = e % n;
+            R s = 0;
 #pragma unroll 6
-          for (int r = 0; r < n; ++r) s += w.V[i * n + r] * w.A[r * n + j];
-          w.VA[e] = s;
-        } else {
-          const int f = e - n * n, i = f / m, j = f % m;
-          R s = 0;
+            for (int r = 0; r < n; ++r) s += w.V[i * n + r] * w.A[r * n + j];
+            w.VA[e] = s;
+          } else {
+            const int f = e - n * n, i = f / m, j = f % m;
+            R s = 0;
 #pragma unroll 6
-          for (int r = 0; r < n; ++r) s += w.V[i * n + r] * w.Bm[r * m + j];
-          w.VB[f] = s;
+            for (int r = 0; r < n; ++r) s += w.V[i * n + r] * w.Bm[r * m + j];
+            w.VB[f] = s;
+          }
         }
-      }
-    g.sync();
-    // Q terms; Q_xx (upper triangle, mirrored) overwrites V
-    if (act)
-      for (int e = g.lane; e < NT + m * n + m * m + n + m; e += G) {
-        if (e < NT) {
-          // unrank e -> (i, j), i <= j, row-major over the upper triangle
-          int i, j;
-          unrank_upper(e, i, j);
-          R s = w.lxx[i * n + j];
+      g.sync();
+      // Q terms; Q_xx (upper triangle, mirrored) overwrites V
+      if (act)
+        for (int e = g.lane; e < NT + m * n + m * m + n + m; e += G) {
+          if (e < NT) {
+            // unrank e -> (i, j), i <= j, row-major over the upper triangle
+            int i, j;
+            unrank_upper(e, i, j);
+            R s = w.lxx[i * n + j];
 #pragma unroll 6
-          for (int r = 0; r < n; ++r) s += w.A[r * n + i] * w.VA[r * n + j];
-          w.V[i * n + j] = s;
-          w.V[j * n + i] = s;
-        } else if (e < NT + m * n) {
-          const int f = e - NT, i = f / n, j = f % n;
-          R s = 0;
+            for (int r = 0; r < n; ++r) s += w.A[r * n + i] * w.VA[r * n + j];
+            w.V[i * n + j] = s;
+            w.V[j * n + i] = s;
+          } else if (e < NT + m * n) {
+            const int f = e - NT, i = f / n, j = f % n;
+            R s = 0;
 #pragma unroll 6
-          for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VA[r * n + j];
-          w.Qux[f] = s;                                 // Q_ux (l_ux = 0)
-        } else if (e < NT + m * n + m * m) {
-          const int f = e - NT - m * n, i = f / m, j = f % m;
-          R s = w.luu[f];
+            for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VA[r * n + j];
+            w.Qux[f] = s;                                 // Q_ux (l_ux = 0)
+          } else if (e < NT + m * n + m * m) {
+            const int f = e - NT - m * n, i = f / m, j = f % m;
+            R s = w.luu[f];
 #pragma unroll 6
-          for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VB[r * m + j];
-          w.Quu[f] = (double)s;                         // Q_uu
-          w.Quf[f] = s;
-        } else if (e < NT + m * n + m * m + n) {
-          const int i = e - NT - m * n - m * m;
-          R s = w.lx[i];
+            for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VB[r * m + j];
+            w.Quu[f] = (double)s;                         // Q_uu
+            w.Quf[f] = s;
+          } else if (e < NT + m * n + m * m + n) {
+            const int i = e - NT - m * n - m * m;
+            R s = w.lx[i];
 #pragma unroll 6
-          for (int r = 0; r < n; ++r) s += w.A[r * n + i] * w.v[r];
-          w.Qx[i] = s;
-        } else {
-          const int i = e - NT - m * n - m * m - n;
-          R s = w.lu[i];
+            for (int r = 0; r < n; ++r) s += w.A[r * n + i] * w.v[r];
+            w.Qx[i] = s;
+          } else {
+            const int i = e - NT - m * n - m * m - n;
+            R s = w.lu[i];
 #pragma unroll 6
-          for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.v[r];
-          w.Qu[i] = s;
+            for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.v[r];
+            w.Qu[i] = s;
+          }
         }
+      g.sync();
+      TO_TICK(2);
+      if (act && g.lane == 0) {
+        chol_group(w, a.lm, mu_lm);
       }
-    g.sync();
-    TO_TICK(2);
-    if (act && g.lane == 0) {
-      chol_group(w, a.lm, mu_lm);
-    }
-    g.sync();
+      g.sync();
     }
     const int flag = act ? w.flag : 0;
     if (act && flag < 2)

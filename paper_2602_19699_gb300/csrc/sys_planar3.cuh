@@ -9,8 +9,10 @@
 //     link k, P_i: position of joint i),
 //   * semi-implicit Euler  qd+ = qd + dt qdd,  q+ = q + dt qd+.
 // Derivatives: d qdd / d(q, qd) = -M^{-1} d ID(q, qd, qdd) / d(q, qd) with the
-// directional derivative of the Newton-Euler recursion written out by hand
-// (one direction per lane), d qdd / d tau = M^{-1}.
+// directional derivative of the Newton-Euler recursion written out by hand,
+// d qdd / d tau = M^{-1}: one direction per lane of a group (derivs), or all
+// six and the columns of M^{-1} on one lane (derivs_lane), which the solver
+// runs for every knot before the backward pass and stores (kStoredDerivs).
 #pragma once
 #include "common.cuh"
 
