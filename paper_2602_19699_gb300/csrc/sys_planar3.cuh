@@ -10,9 +10,9 @@
 //   * semi-implicit Euler  qd+ = qd + dt qdd,  q+ = q + dt qd+.
 // Derivatives: d qdd / d(q, qd) = -M^{-1} d ID(q, qd, qdd) / d(q, qd) with the
 // directional derivative of the Newton-Euler recursion written out by hand,
-// d qdd / d tau = M^{-1}: one direction per lane of a group (derivs), or all
-// six and the columns of M^{-1} on one lane (derivs_lane), which the solver
-// runs for every knot before the backward pass and stores (kStoredDerivs).
+// d qdd / d tau = M^{-1}: all six directions and the columns of M^{-1} on one
+// lane (derivs_lane), which the solver runs for every knot before the
+// backward pass and stores (kStoredDerivs).
 #pragma once
 #include "common.cuh"
 
@@ -188,55 +188,11 @@ struct SysPlanar3 {
   }
 
 
-  // Columns of [A | B] and the clipped running-cost derivatives.  Every lane
-  // evaluates the shared primal (kinematics, M's factor, qdd); lanes 0..5
-  // then differentiate along x_c (one tangent Newton-Euler pass each), the
-  // next lanes form the columns of M^{-1} for B, and one lane the cost terms.
-  // Groups of 8 put two B columns on lane 6 and the third with the cost on
-  // lane 7.
-  template <class R, int G>
-  TO_DEV static void derivs(const Planar3Params<R>& P, const Group<G>& g, const R* x, const R* u, R eps, R* A,
-                            R* B, R* lxx, R* lx, R* luu, R* lu, R*) {
-    static_assert(G >= 8, "planar3 derivatives need at least 8 lanes");
-    const int lane = g.lane;
-    const R dt = P.dt;
-    Kin<R> k;
-    kinematics(P, x, k);
-    R qdd[3], L[9], d[3];
-    forward_dynamics(P, k, x + 3, u, qdd, L);
-    if (lane < n) {
-      R dq[3] = {0, 0, 0}, dqd[3] = {0, 0, 0}, tau[3], dtau[3];
-      if (lane < 3) dq[lane] = 1; else dqd[lane - 3] = 1;
-      rnea<R, true>(P, k, x + 3, qdd, tau, dq, dqd, dtau);
-      chol3_solve(L, dtau, d);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const R eq = (lane == i) ? R(1) : R(0);          // dq_i / dx_c
-        const R ev = (lane == 3 + i) ? R(1) : R(0);      // dqd_i / dx_c
-        const R dv = ev - dt * d[i];                      // d qd+_i / dx_c  (d qdd = -M^{-1} d ID)
-        A[(3 + i) * n + lane] = dv;
-        A[i * n + lane] = eq + dt * dv;
-      }
-    } else {
-      const int c0 = (G >= 16) ? lane - n : (lane == n ? 0 : 2);
-      const int c1 = (G >= 16) ? c0 : (lane == n ? 1 : 2);
-      for (int c = c0; c <= c1 && c < m; ++c) {
-        R e[3] = {0, 0, 0};
-        e[c] = 1;
-        chol3_solve(L, e, d);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          B[(3 + i) * m + c] = dt * d[i];
-          B[i * m + c] = dt * dt * d[i];
-        }
-      }
-    }
-    const int cost_lane = (G >= 16) ? n + m : G - 1;
-    if (lane == cost_lane) running_derivs_k(P, k, u, eps, lxx, lx, luu, lu);
-  }
-
-  // the same on one lane (single-lane groups): one primal, the six tangent
-  // passes, the three columns of M^{-1} and the cost terms in turn
+  // Columns of [A | B] and the clipped running-cost derivatives on one lane:
+  // the primal (kinematics, M's factor, qdd), then the tangent Newton-Euler
+  // pass along each x_c, the three columns of M^{-1} for B, and the cost
+  // terms.  The solver runs it for every knot before the backward pass (one
+  // knot per lane, blocks stored) and inside single-lane groups.
   template <class R>
   TO_DEV static void derivs_lane(const Planar3Params<R>& P, const R* x, const R* u, R eps, R* A, R* B, R* lxx,
                                  R* lx, R* luu, R* lu) {
