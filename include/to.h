@@ -211,8 +211,13 @@ int tocreate_problem(const to_problem_desc* desc, to_problem* out);
 void todestroy_problem(to_problem p);
 
 /* Allocate the device workspace of a batch able to hold B_max instances whose
- * horizons sum (over T+1) to at most knots_max.  Reusing one batch object for
- * many solves keeps allocation out of the solve.  Errors: TO_ERR_ARG,
+ * horizons sum (over T+1) to at most knots_max.  Per knot it holds the knot
+ * records of min(group_lanes, 16) + 1 trajectory slots, the gain record and,
+ * for the planar arm and the rigid trees, a derivative scratch (the planar
+ * arm's stored derivative block, 108 elements; the rigid trees' n_sub stored
+ * substep primals, about 6 KB each in float32 for the quadruped); elements
+ * are float64 or float32 by opts->prec.  Reusing one batch object for many
+ * solves keeps allocation out of the solve.  Errors: TO_ERR_ARG,
  * TO_ERR_BUDGET (workspace above opts->hbm_budget_bytes), TO_ERR_CUDA. */
 int tocreate_batch(to_problem p, int B_max, long long knots_max, const to_solver_opts* opts, to_batch* out);
 void tofree_batch(to_batch b);
