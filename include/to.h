@@ -204,7 +204,11 @@ enum { TO_REG_CLIP = 0, TO_REG_LM = 1 };
  * autotuned launch shape. */
 void to_default_opts(to_solver_opts* opts);
 
-/* Validate the description, parse params into the system's device layout and
+/* One instance family of the OCP of Sec. II, Eq. 1: the system's dynamics
+ * f_k, running cost l_k and terminal cost l_T (params), the horizon bound
+ * T_max and, optionally, the actor policy whose rollout is the warm start
+ * (Sec. II; Sec. III-D for the policy's use as initial guess).
+ * Validate the description, parse params into the system's device layout and
  * upload it (plus the actor weights).  Errors: TO_ERR_ARG (shape, layout or a
  * system whose joint structure the GPU model does not cover), TO_ERR_CUDA. */
 int tocreate_problem(const to_problem_desc* desc, to_problem* out);
@@ -222,7 +226,12 @@ void todestroy_problem(to_problem p);
 int tocreate_batch(to_problem p, int B_max, long long knots_max, const to_solver_opts* opts, to_batch* out);
 void tofree_batch(to_batch b);
 
-/* Solve B instances.  x0: host B x n; T: host B horizons in [1, T_max];
+/* Solve B instances of Eq. 1 (Sec. II), one per initial state x_init, with
+ * the iLQR iteration of Sec. II and Sec. IV-B (backward pass with clipped cost
+ * Hessians and the Q_uu Cholesky, then the line search) under the
+ * per-instance iteration budget of Sec. IV-A; the batched form is the paper's
+ * TO of many problems at once on the GPU (Sec. IV).
+ * x0: host B x n; T: host B horizons in [1, T_max];
  * U_init: host B x T_max x m initial controls or NULL (zero controls, or the
  * actor warm start when the problem has actor weights).  The work is enqueued
  * on cuda_stream (a cudaStream_t, NULL = the legacy default stream) and the
@@ -241,7 +250,11 @@ int tosolve_batch(to_problem p, int B, const double* x0, const int* T, const dou
 int tosolve_batch_device(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U_init,
                          const int* d_forced, const to_solver_opts* opts, void* cuda_stream);
 
-/* Copy results of the last solve to the host (synchronises the batch's
+/* The solution of the last solve (Sec. II): the optimised trajectories X, U
+ * and final cost J of Eq. 1, and, with want_vx, the value gradient V_x of the
+ * DDP backward pass at the returned iterate and its feedback gains K, the
+ * outputs the paper hands to critic training (Sec. II).
+ * Copy results of the last solve to the host (synchronises the batch's
  * stream).  X: B x (T_max+1) x n, U: B x T_max x m, J, iters, status: B;
  * Vx: B x (T_max+1) x n and K: B x T_max x m x n (need want_vx; may be NULL);
  * any output pointer may be NULL.  T_max is the problem's. */
@@ -338,7 +351,11 @@ int toserve_replay(to_server s, int n_req, const double* arrival_s, const int* p
  * (B x (T_max+1) x n float64) and d_U (B x T_max x m float64) may be NULL.
  * opts may not set forced_alpha, want_vx or profile_phases
  * (TO_ERR_UNSUPPORTED).  The work is enqueued on cuda_stream; results are
- * ready when the stream reaches them.
+ * ready when the stream reaches them.  A horizon outside [1, T_max] is found
+ * on the device (the host never reads d_T): then every instance gets
+ * TO_ST_NONFINITE, d_J is NaN, d_X and d_U (if given) are NaN, and nothing
+ * else is computed.  The call must come from the device the problem was
+ * created on (TO_ERR_ARG otherwise).
  *
  * The first call on each device looks up the array's device address (with
  * that device current), so make that first call before any stream capture.
