@@ -114,20 +114,33 @@ __global__ void prepare_kernel(int B, const int* __restrict__ T, int T_max, long
   if (tid == 0) *err = bad;
 }
 
-// results to instance-major float64 arrays with the padding of include/to.h
+// results to instance-major float64 arrays with the padding of include/to.h.
+// A batch that the prepare kernel rejected (*err set: a horizon outside
+// [1, T_max] or more knots than the workspace) ran no solve, so its offsets
+// and slots are not valid: every output is NaN and nothing is read.  The
+// horizon and slot are clamped to their ranges before use either way.
 __global__ void gather_kernel(int B, int T_max, int n, int m, int RS, int GS, int NS, int rbytes,
                               const long long* __restrict__ toff, const int* __restrict__ T,
                               const int* __restrict__ slot,
                               const void* __restrict__ traj, const void* __restrict__ gains,
                               const double* __restrict__ vx, double* __restrict__ X, double* __restrict__ U,
-                              double* __restrict__ Vx, double* __restrict__ K) {
+                              double* __restrict__ Vx, double* __restrict__ K, const int* __restrict__ err) {
   const long long total = (long long)B * (T_max + 1);
+  const bool rejected = err && *err;
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(t / (T_max + 1));
     const int k = (int)(t % (T_max + 1));
-    const int Tb = T[b];
+    if (rejected) {
+      if (X) for (int i = 0; i < n; ++i) X[t * n + i] = qnan;
+      if (U && k < T_max) for (int i = 0; i < m; ++i) U[((long long)b * T_max + k) * m + i] = qnan;
+      if (Vx) for (int i = 0; i < n; ++i) Vx[t * n + i] = qnan;
+      if (K && k < T_max) for (int i = 0; i < m * n; ++i) K[((long long)b * T_max + k) * m * n + i] = qnan;
+      continue;
+    }
+    const int Tb = min(max(T[b], 0), T_max);
     const long long base = toff[b];
-    const int sl = slot[b];
+    const int sl = min(max(slot[b], 0), NS - 1);
     const long long xr = ((base + min(k, Tb)) * NS + sl) * RS;
     auto rd = [&](const void* p, long long idx) -> double {
       return rbytes == 8 ? reinterpret_cast<const double*>(p)[idx] : (double)reinterpret_cast<const float*>(p)[idx];
@@ -437,6 +450,14 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   to_problem p = b->p;
   const SysOps* ops = p->ops;
   const int prec = o->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
+  // the problem's parameters and actor weights live on the device that was
+  // current when it was created; a launch from another device would hand the
+  // kernel another GPU's pointers
+  int cur_dev = -1;
+  TO_CK(cudaGetDevice(&cur_dev));
+  if (cur_dev != p->device)
+    return fail(TO_ERR_ARG, "solve: the current device is " + std::to_string(cur_dev) + ", the problem was created on " +
+                                std::to_string(p->device));
   // a serving kernel, or a member of a multi-system graph, takes its share of
   // the resident CTAs, so the kernels of the other problems run beside it
   const double frac = serve ? serve->grid_frac : b->grid_frac;
@@ -514,7 +535,8 @@ int to_enqueue_gather(to_batch b, int B, const int* d_T, double* d_X, double* d_
   const int pi = b->prec == TO_FP64 ? 0 : 1;
   const int NS = std::min(b->G, kLsWidth) + 1;
   gather_kernel<<<1024, 256, 0, s>>>(B, p->T_max, p->n, p->m, p->ops->rs[pi], p->ops->gs[pi], NS, pi == 0 ? 8 : 4,
-                                     b->toff, d_T, b->slot, b->traj, b->gains, nullptr, d_X, d_U, nullptr, nullptr);
+                                     b->toff, d_T, b->slot, b->traj, b->gains, nullptr, d_X, d_U, nullptr, nullptr,
+                                     b->err);
   TO_CK(cudaGetLastError());
   return TO_OK;
 }
@@ -619,7 +641,7 @@ int toget_trajectories(to_batch b, double* X, double* U, double* J, int* iters, 
     gather_kernel<<<1024, 256, 0, b->stream>>>(B, p->T_max, p->n, p->m, rs, gs, NS, rbytes, b->toff, b->last_T, b->slot,
                                                b->traj,
                                                b->gains, b->vx, X ? b->gX : nullptr, U ? b->gU : nullptr,
-                                               Vx ? b->gV : nullptr, K ? b->gK : nullptr);
+                                               Vx ? b->gV : nullptr, K ? b->gK : nullptr, b->err);
     TO_CK(cudaGetLastError());
   }
   if (X) TO_CK(cudaMemcpyAsync(X, b->gX, nX * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
@@ -728,6 +750,8 @@ int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_
   // the device address of the array: once per device, with that device current
   int dev = 0;
   TO_CK(cudaGetDevice(&dev));
+  if (dev != p->device)
+    return fail(TO_ERR_ARG, "tosolve_batch_noalloc: the current device is not the one the problem was created on");
   if (dev < 0 || dev >= kMaxDevices) return fail(TO_ERR_UNSUPPORTED, "tosolve_batch_noalloc: device index too large");
   unsigned char* base = nullptr;
   {
@@ -788,7 +812,7 @@ int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_
   if (d_X || d_U) {
     const int NS = std::min(w.G, kLsWidth) + 1;
     gather_kernel<<<1024, 256, 0, s>>>(B, p->T_max, p->n, p->m, ops->rs[pi], ops->gs[pi], NS, elem, w.toff, d_T,
-                                       w.slot, w.traj, w.gains, nullptr, d_X, d_U, nullptr, nullptr);
+                                       w.slot, w.traj, w.gains, nullptr, d_X, d_U, nullptr, nullptr, w.err);
     TO_CK(cudaGetLastError());
   }
   return TO_OK;

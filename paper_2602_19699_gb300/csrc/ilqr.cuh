@@ -204,7 +204,13 @@ struct Solver {
   static constexpr int kLo = Layout<Sys, R>::kLo;
   static constexpr int NF = n + m + m * (n + 1) + kLo;    // forward record: x, u, K, k, x_lo
   static constexpr int PF = (NF + G - 1) / G;             // prefetch registers per lane (forward)
-  static constexpr int PB = (n + m + G - 1) / G;          // prefetch registers per lane (backward)
+  // prefetch registers per lane (backward): the knot record x_k, u_k, or,
+  // for systems that store a derivative block per knot, that block
+  template <class S> static constexpr int bwd_prefetch_elems() {
+    if constexpr (S::kStoredDerivs) return S::kDerivStride;
+    else return S::n + S::m;
+  }
+  static constexpr int PB = (bwd_prefetch_elems<Sys>() + G - 1) / G;
   static constexpr int LW = G < kLsWidth ? G : kLsWidth;   // step sizes per line-search round
   static constexpr int NS = LW + 1;                        // trajectory slots per knot
   static constexpr int kRounds = (kMaxAlpha + LW - 1) / LW; // most line-search rounds
@@ -430,18 +436,31 @@ struct Solver {
     // (a system whose derivative step holds group barriers has groups of a
     // whole warp or CTA, so act is uniform over every barrier's scope)
     if constexpr (Sys::kStoredDerivs) {
-      // the knot's stored block: A, B, l_xx, l_x, l_uu, l_u
+      // the knot's stored block (A, B, l_xx, l_x, l_uu, l_u), prefetched into
+      // pb while the previous knot computed; then the next knot's block is
+      // fetched into pb (kprim: the next knot's block)
       constexpr int DS = Sys::kDerivStride;
-      if (act)
-        for_each_lane<DS>(g, [&](int e) {
-          const R v = kprim[e];
+      if (act) {
+#pragma unroll
+        for (int s = 0; s < PB; ++s) {
+          const int e = g.lane + s * G;
+          const R v = pb[s];
+          if (e >= DS) continue;
           if (e < n * n) w.A[e] = v;
           else if (e < n * n + n * m) w.Bm[e - n * n] = v;
           else if (e < 2 * n * n + n * m) w.lxx[e - n * n - n * m] = v;
           else if (e < 2 * n * n + n * m + n) w.lx[e - 2 * n * n - n * m] = v;
           else if (e < 2 * n * n + n * m + n + m * m) w.luu[e - 2 * n * n - n * m - n] = v;
           else w.lu[e - 2 * n * n - n * m - n - m * m] = v;
-        });
+        }
+      }
+      if (act_next) {
+#pragma unroll
+        for (int s = 0; s < PB; ++s) {
+          const int e = g.lane + s * G;
+          if (e < DS) pb[s] = kprim[e];
+        }
+      }
     } else if (act) {
       if constexpr (Sys::kKnotParallel)
         Sys::template derivs_staged<R, G>(P, g, w.xk, w.uk, eps, w.A, w.Bm, w.lxx, w.lx, w.luu, w.lu, w.sx, kprim);
@@ -1008,11 +1027,13 @@ struct Solver {
               if (a.vx && a.want_vx)
                 for (int i = 0; i < n; ++i) a.vx[(base + T) * n + i] = (double)w.v[i];
             }
-            const R* r = rec(traj, base, T - 1, cur);
+            if constexpr (!Sys::kStoredDerivs) {
+              const R* r = rec(traj, base, T - 1, cur);
 #pragma unroll
-            for (int s = 0; s < PB; ++s) {
-              const int e = g.lane + s * G;
-              if (e < n + m) pb[s] = r[e];
+              for (int s = 0; s < PB; ++s) {
+                const int e = g.lane + s * G;
+                if (e < n + m) pb[s] = r[e];
+              }
             }
           }
           if constexpr (Sys::kStoredDerivs) {
@@ -1048,13 +1069,27 @@ struct Solver {
               }
           }
           g.sync();
+          if constexpr (Sys::kStoredDerivs) {
+            // the last knot's stored block (written above by the group's lanes)
+            if (bw) {
+              const R* d = reinterpret_cast<const R*>(a.dscr) + (base + T - 1) * a.kscr;
+#pragma unroll
+              for (int s = 0; s < PB; ++s) {
+                const int e = g.lane + s * G;
+                if (e < Sys::kDerivStride) pb[s] = d[e];
+              }
+            }
+          }
           TO_TICK(1);
           for (int k = kmax - 1; k >= 0; --k) {
             const bool act = bw && k < T;
             const bool act_next = bw && k >= 1 && k - 1 < T;
             const long long kk = base + (act ? k : 0);
             const R* rn = rec(traj, base, act_next ? k - 1 : 0, cur);
-            const R* kprim = (Sys::kKnotParallel || Sys::kStoredDerivs) ? reinterpret_cast<const R*>(a.dscr) + kk * a.kscr
+            // rigid trees: the knot's stored substep primals; planar arm: the
+            // next knot's stored derivative block (this knot's is in pb)
+            const long long kd = Sys::kStoredDerivs ? base + (act_next ? k - 1 : 0) : kk;
+            const R* kprim = (Sys::kKnotParallel || Sys::kStoredDerivs) ? reinterpret_cast<const R*>(a.dscr) + kd * a.kscr
                                                                           : nullptr;
             const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, gains + kk * GS,
                                         (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, mu_lm, timer, tlast,
@@ -1291,6 +1326,6 @@ __global__ void gather_kernel(int B, int T_max, int n, int m, int RS, int GS, in
                               const int* __restrict__ slot,
                               const void* __restrict__ traj, const void* __restrict__ gains,
                               const double* __restrict__ vx, double* __restrict__ X, double* __restrict__ U,
-                              double* __restrict__ Vx, double* __restrict__ K);
+                              double* __restrict__ Vx, double* __restrict__ K, const int* __restrict__ err);
 
 }  // namespace to

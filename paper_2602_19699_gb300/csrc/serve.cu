@@ -311,7 +311,7 @@ int topoll(to_server s, uint64_t req_id, double* X, double* U, double* J, int* i
     gather_kernel<<<64, 256, 0, L.copy>>>(1, p->T_max, p->n, p->m, p->ops->rs[pr], p->ops->gs[pr], NS,
                                           pr == 0 ? 8 : 4, L.seat_toff + r.seat, L.seat_T + r.seat,
                                           L.b->slot + r.seat, L.b->traj, L.b->gains, nullptr, X ? L.gX : nullptr,
-                                          U ? L.gU : nullptr, nullptr, nullptr);
+                                          U ? L.gU : nullptr, nullptr, nullptr, nullptr);
     SV_CK(cudaGetLastError());
     if (X) SV_CK(cudaMemcpyAsync(X, L.gX, sizeof(double) * (p->T_max + 1) * p->n, cudaMemcpyDeviceToHost, L.copy));
     if (U) SV_CK(cudaMemcpyAsync(U, L.gU, sizeof(double) * p->T_max * p->m, cudaMemcpyDeviceToHost, L.copy));

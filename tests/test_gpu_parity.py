@@ -289,6 +289,9 @@ def test_invalid_horizon_rejected_on_device(P):
     torch.cuda.synchronize()
     r = P.toget_trajectories(bt, X=False, U=False)
     assert np.all(r["status"] == P.TO_ST_NONFINITE)
+    # the gather reads no offset or slot of the rejected batch: X and U are NaN
+    r = P.toget_trajectories(bt)
+    assert np.all(np.isnan(r["X"])) and np.all(np.isnan(r["U"]))
 
 
 def test_empty_batch_and_knot_capacity(P, oracle_mod):

@@ -113,3 +113,25 @@ def test_noalloc_rigid_trees(P, sysname):
     for key in ("X", "U"):
         a, r = got[key][ok], ref[key][ok]
         assert np.all(np.abs(a - r) <= MIXED_X_TOL * np.maximum(np.abs(r).max(axis=(1, 2), keepdims=True), 1e-300))
+
+
+def test_noalloc_rejected_horizon_reads_nothing(P):
+    """A horizon outside [1, T_max] is caught on the device: every instance
+    ends TO_ST_NONFINITE and the gathered X and U are NaN.  The call comes
+    right after a valid solve, so the static array still holds that solve's
+    offsets and slots; none of them may be read for the rejected batch."""
+    import torch
+    prob = W.planar3(seed=2)
+    problem = P.tocreate_problem(prob.sys, prob.params, 60)
+    opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=5)
+    b = W.make_batch(prob, 16, seed=21, T=(10, 60))
+    x0 = torch.tensor(b.x0, dtype=torch.float64, device="cuda")
+    T = torch.tensor(b.T, dtype=torch.int32, device="cuda")
+    good = _noalloc(P, problem, x0, T, opts)
+    assert np.all(np.isin(good["status"] & 15, [1, 2, 3]))
+    Tbad = b.T.copy()
+    Tbad[5] = 61                                     # T_max + 1
+    got = _noalloc(P, problem, x0, torch.tensor(Tbad, dtype=torch.int32, device="cuda"), opts)
+    assert np.all(got["status"] == P.TO_ST_NONFINITE)
+    assert np.all(np.isnan(got["J"]))
+    assert np.all(np.isnan(got["X"])) and np.all(np.isnan(got["U"]))
