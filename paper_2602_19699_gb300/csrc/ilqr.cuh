@@ -357,7 +357,7 @@ struct Solver {
             r[i] = (float)t;
           }
         } else {
-          const float muf = (float)mu;
+          const float muf = d2f(mu);
 #pragma unroll
           for (int i = 0; i < m; ++i) {
             Acc<float> t;
@@ -404,6 +404,245 @@ struct Solver {
     const int rb = (int)((__fsqrt_rn((float)(8 * eb + 1)) - 1.0f) * 0.5f);   // row counted from the bottom
     i = n - 1 - rb;
     j = n - 1 - (eb - rb * (rb + 1) / 2);
+  }
+
+  // float32 <-> float64 of the solver's own values without the float64 pipe
+  // in mixed mode (plain casts in float64 mode, where they are no-ops)
+  TO_DEV static double to_f64(R x) {
+    if constexpr (sizeof(R) == 4) return f2d(x);
+    else return (double)x;
+  }
+  TO_DEV static R to_R(double x) {
+    if constexpr (sizeof(R) == 4) return d2f(x);
+    else return (R)x;
+  }
+
+  // the same for small n on the integer pipe: walk the rows (no square root)
+  TO_DEV static void unrank_upper_small(int e, int& i, int& j) {
+    int r = e, row = 0;
+#pragma unroll
+    for (int t = 0; t < n - 1; ++t) {
+      const bool next = r >= n - row;
+      r = next ? r - (n - row) : r;
+      row = next ? row + 1 : row;
+    }
+    i = row;
+    j = row + r;
+  }
+
+  // ------------------------------------------------------------------------
+  // float64 Cholesky of Q (+ shift I when kShift) under the pivot test
+  // d_j > delta, with every branch folded: each lane of a group runs it on the
+  // group's Q_uu (a float64 warp instruction occupies the FP64 pipe for the
+  // same time whatever lanes are active, so the copies cost nothing extra and
+  // no lane diverges), and the caller can interleave it with float32 work.
+  // Returns true when every pivot passed the test and, with kSeeded (the
+  // reciprocal pivot roots from rsqrt_newton), lies in the normal float32
+  // range; otherwise the caller redoes the factor on the guarded path, which
+  // decides exactly as before.  The diagonal of L holds 1 / L_jj.
+  // ------------------------------------------------------------------------
+  template <bool kSeeded, bool kShift>
+  TO_DEV static bool chol_nb(const double (&Q)[m * m], double shift, double delta, double (&L)[m * m]) {
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < m; ++j) {
+      double s = Q[j * m + j];
+      if (kShift) s += shift;
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= L[j * m + k] * L[j * m + k];
+      ok = ok & dgt_nonneg(s, delta);
+      if (kSeeded) ok = ok & (__double_as_longlong(s) >= 0x3810000000000000LL);   // s >= FLT_MIN
+      const double r = kSeeded ? rsqrt_newton(s) : rsqrt(s);
+      L[j * m + j] = r;
+#pragma unroll
+      for (int i = j + 1; i < m; ++i) {
+        double t = Q[i * m + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
+        L[i * m + j] = t * r;
+      }
+    }
+    return ok;
+  }
+
+  // ------------------------------------------------------------------------
+  // One backward knot for sub-warp groups (2 <= G < 32), split by columns.
+  //   1. Q_uu and Q_u: lane c forms column c of V B in registers, then
+  //      column c of Q_uu = l_uu + B^T (V B).
+  //   2. Every lane factors the group's Q_uu in float64 (chol_nb) while lane
+  //      j forms column j of V A in registers and from it column j of Q_xx,
+  //      of Q_ux and Q_x[j]: no barrier between the products, no branch, and
+  //      no lane waits for a leader's float64 chain.  Q_xx goes to the V A
+  //      buffer, so V stays readable by every lane meanwhile.
+  //   3. Gain columns from each lane's own copy of the factor.
+  //   4. V_xx <- sym(Q_xx + Q_ux^T K), V_x <- Q_x + Q_ux^T k, gains to memory.
+  // The arithmetic (and its summation order) is that of the single-pass
+  // form; lanes past the last column recompute the last one and store
+  // nothing, so the code of each phase is straight-line.
+  // ------------------------------------------------------------------------
+  TO_DEV static int backward_cols(const Group<G>& g, W& w, bool act, const SolveArgs& a, R* grec, double* vxrec,
+                                  double mu_lm, bool timer, long long& tlast) {
+    static_assert(G >= 2 && G < 32, "sub-warp groups");
+    constexpr int NT = n * (n + 1) / 2;
+    R* QX = w.VA;                                         // Q_xx, full (mirrored)
+    // 1. Q_uu (float64 and R copies) and Q_u
+#pragma unroll
+    for (int s = 0; s < (m + G - 1) / G; ++s) {
+      const int c0 = g.lane + s * G;
+      const bool st = act && c0 < m;
+      const int c = c0 < m ? c0 : m - 1;
+      R vb[n];
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        R t = 0;
+#pragma unroll
+        for (int r = 0; r < n; ++r) t += w.V[i * n + r] * w.Bm[r * m + c];
+        vb[i] = t;
+      }
+#pragma unroll
+      for (int i = 0; i < m; ++i) {
+        R t = w.luu[i * m + c];
+#pragma unroll
+        for (int r = 0; r < n; ++r) t += w.Bm[r * m + i] * vb[r];
+        if (st) {
+          w.Quu[i * m + c] = to_f64(t);
+          w.Quf[i * m + c] = t;
+        }
+      }
+      R t = w.lu[c];
+#pragma unroll
+      for (int r = 0; r < n; ++r) t += w.Bm[r * m + c] * w.v[r];
+      if (st) w.Qu[c] = t;
+    }
+    g.sync();
+    TO_TICK(2);
+    // 2. the float64 factor on every lane, interleaved with the column products
+    double Lr[m * m];
+    double mu = 0;
+    bool ok;
+    constexpr bool kSeed = sizeof(R) == 4;
+    {
+      double Q[m * m];
+      R mxr = R(0);
+#pragma unroll
+      for (int i = 0; i < m; ++i) mxr = max_abs(mxr, w.Quf[i * m + i]);
+#pragma unroll
+      for (int i = 0; i < m; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) Q[i * m + j] = w.Quu[i * m + j];
+      const double mx = to_f64(mxr);
+      auto cols = [&]() {
+#pragma unroll
+        for (int s = 0; s < (n + G - 1) / G; ++s) {
+          const int j0 = g.lane + s * G;
+          const bool st = act && j0 < n;
+          const int j = j0 < n ? j0 : n - 1;
+          R va[n];
+#pragma unroll
+          for (int i = 0; i < n; ++i) {
+            R t = 0;
+#pragma unroll
+            for (int r = 0; r < n; ++r) t += w.V[i * n + r] * w.A[r * n + j];
+            va[i] = t;
+          }
+#pragma unroll
+          for (int i = 0; i < n; ++i) {
+            R t = w.lxx[i * n + j];
+#pragma unroll
+            for (int r = 0; r < n; ++r) t += w.A[r * n + i] * va[r];
+            if (st) QX[i * n + j] = t;                    // the whole column: Q_xx as the oracle forms it
+          }
+#pragma unroll
+          for (int i = 0; i < m; ++i) {
+            R t = 0;
+#pragma unroll
+            for (int r = 0; r < n; ++r) t += w.Bm[r * m + i] * va[r];
+            if (st) w.Qux[i * n + j] = t;                 // Q_ux (l_ux = 0)
+          }
+          R t = w.lx[j];
+#pragma unroll
+          for (int r = 0; r < n; ++r) t += w.A[r * n + j] * w.v[r];
+          if (st) w.Qx[j] = t;
+        }
+      };
+      if (a.lm) {
+        mu = mu_lm;
+        ok = chol_nb<kSeed, true>(Q, mu, 1e-12 * (mx + mu), Lr);
+        cols();
+        ok = ok & (mxr == mxr) & (mxr <= R(3.0e38));
+      } else {
+        ok = chol_nb<kSeed, false>(Q, 0.0, 1e-12 * mx, Lr);
+        cols();
+        ok = ok & (mxr > R(0)) & (mxr <= R(3.0e38));
+      }
+    }
+    // the guarded path (a failed pivot test, or a pivot outside the seed's
+    // range): the float64 factor with the shift schedule, as in factor()
+    R Lf[m * m];
+    int flag = 0;
+    if (!ok) {
+      flag = factor(w.Quu, w.Quf, a.lm, mu_lm, Lr, Lf, mu);
+    } else {
+#pragma unroll
+      for (int i = 0; i < m; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) Lf[i * m + j] = to_R(Lr[i * m + j]);
+    }
+    g.sync();
+    // 3. gain columns (c < n: K[:, c]; c == n: k)
+    if (act && flag < 2)
+      for (int c = g.lane; c <= n; c += G) gain_col(c, a.refine, w.Qux, w.Qu, w.Quu, w.Quf, Lr, Lf, mu, w.K, w.kf);
+    g.sync();
+    TO_TICK(3);
+    // 4. lane j: column j of V_xx <- sym(Q_xx + Q_ux^T K) and V_x[j] <-
+    //    Q_x[j] + Q_ux[:, j]^T k (Q_xx is read from its own buffer, so V is
+    //    written in place without a barrier); entry (i, j) and entry (j, i)
+    //    take the same operations in the same order, so V stays exactly
+    //    symmetric.  The gain record goes to memory in 16-byte vectors.
+#pragma unroll
+    for (int s = 0; s < (n + G - 1) / G; ++s) {
+      const int j0 = g.lane + s * G;
+      const bool st = act && j0 < n;
+      const int j = j0 < n ? j0 : n - 1;
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        R sij = QX[i * n + j], sji = QX[j * n + i];
+#pragma unroll
+        for (int r = 0; r < m; ++r) {
+          sij += w.Qux[r * n + i] * w.K[r * n + j];
+          sji += w.Qux[r * n + j] * w.K[r * n + i];
+        }
+        const R t = R(0.5) * (sij + sji);                  // a + b == b + a: (j, i) gets the same bits
+        if (st) w.V[i * n + j] = t;
+      }
+      R t = w.Qx[j];
+#pragma unroll
+      for (int r = 0; r < m; ++r) t += w.Qux[r * n + j] * w.kf[r];
+      if (st) {
+        w.v[j] = t;
+        if (vxrec) vxrec[j] = (double)t;
+      }
+    }
+    {
+      constexpr int kV = 16 / (int)sizeof(R), NV = GS / kV;   // K then k, adjacent in W and in memory; then padding
+      static_assert(GS % kV == 0, "gain record in whole vectors");
+#pragma unroll
+      for (int s = 0; s < (NV + G - 1) / G; ++s) {
+        const int v = g.lane + s * G;
+        if (act && v < NV) {
+          R o[kV];
+#pragma unroll
+          for (int q = 0; q < kV; ++q) {
+            const int f = v * kV + q;
+            o[q] = f < m * (n + 1) ? w.K[f] : R(0);
+          }
+          st16(grec + v * kV, o);
+        }
+      }
+    }
+    g.sync();
+    TO_TICK(4);
+    return act ? flag : 0;
   }
 
   // ------------------------------------------------------------------------
@@ -469,84 +708,10 @@ struct Solver {
     }
     g.sync();
     TO_TICK(1);
-    constexpr int NT = n * (n + 1) / 2;
     if constexpr (G >= 2 && G < 32) {
-      // Several groups per warp: V B, then Q_uu and Q_u; then each group's
-      // leader factors Q_uu in float64 while its other lanes form V A and the
-      // remaining Q terms (the leader's float64 chain and their float32
-      // products are independent until the gains).  Measured 4 % faster on
-      // the planar arm's 8-lane groups; with one group per warp (32 lanes)
-      // the single-pass order below was faster.
-      if (act)
-        for (int f = g.lane; f < n * m; f += G) {
-          const int i = f / m, j = f % m;
-          R s = 0;
-#pragma unroll 6
-          for (int r = 0; r < n; ++r) s += w.V[i * n + r] * w.Bm[r * m + j];
-          w.VB[f] = s;
-        }
-      g.sync();
-      if (act)
-        for (int e = g.lane; e < m * m + m; e += G) {
-          if (e < m * m) {
-            const int i = e / m, j = e % m;
-            R s = w.luu[e];
-#pragma unroll 6
-            for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VB[r * m + j];
-            w.Quu[e] = (double)s;                         // Q_uu
-            w.Quf[e] = s;
-          } else {
-            const int i = e - m * m;
-            R s = w.lu[i];
-#pragma unroll 6
-            for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.v[r];
-            w.Qu[i] = s;
-          }
-        }
-      g.sync();
-      TO_TICK(2);
-      if (g.lane == 0) {
-        if (act) chol_group(w, a.lm, mu_lm);
-      } else {
-        constexpr int L = G - 1;                          // the non-leader lanes of a group
-        const int l = g.lane - 1;
-        if (act)
-          for (int e = l; e < n * n; e += L) {
-            const int i = e / n, j = e % n;
-            R s = 0;
-#pragma unroll 6
-            for (int r = 0; r < n; ++r) s += w.V[i * n + r] * w.A[r * n + j];
-            w.VA[e] = s;
-          }
-        __syncwarp(kNonLeaders);                          // every non-leader lane of the warp, act or not
-        if (act)
-          for (int e = l; e < NT + m * n + n; e += L) {
-            if (e < NT) {
-              // Q_xx (upper triangle, mirrored) overwrites V
-              int i, j;
-              unrank_upper(e, i, j);
-              R s = w.lxx[i * n + j];
-#pragma unroll 6
-              for (int r = 0; r < n; ++r) s += w.A[r * n + i] * w.VA[r * n + j];
-              w.V[i * n + j] = s;
-              w.V[j * n + i] = s;
-            } else if (e < NT + m * n) {
-              const int f = e - NT, i = f / n, j = f % n;
-              R s = 0;
-#pragma unroll 6
-              for (int r = 0; r < n; ++r) s += w.Bm[r * m + i] * w.VA[r * n + j];
-              w.Qux[f] = s;                                 // Q_ux (l_ux = 0)
-            } else {
-              const int i = e - NT - m * n;
-              R s = w.lx[i];
-#pragma unroll 6
-              for (int r = 0; r < n; ++r) s += w.A[r * n + i] * w.v[r];
-              w.Qx[i] = s;
-            }
-          }
-      }
-      g.sync();
+      return backward_cols(g, w, act, a, grec, vxrec, mu_lm, timer, tlast);
     } else {
+    constexpr int NT = n * (n + 1) / 2;
       // V A and V B
       if (act)
         for (int e = g.lane; e < n * n + n * m; e += G) {
@@ -610,7 +775,6 @@ struct Solver {
         chol_group(w, a.lm, mu_lm);
       }
       g.sync();
-    }
     const int flag = act ? w.flag : 0;
     if (act && flag < 2)
       for (int c = g.lane; c <= n; c += G) gain_column(w, c, a.refine);
@@ -647,6 +811,7 @@ struct Solver {
     g.sync();
     TO_TICK(4);
     return flag;
+    }
   }
 
   // ------------------------------------------------------------------------
