@@ -580,7 +580,7 @@ struct Solver {
     // range): the float64 factor with the shift schedule, as in factor()
     R Lf[m * m];
     int flag = 0;
-    if (!ok) {
+    if (!ok && act) {          // (an idle group's stale Q_uu takes no guarded retries)
       flag = factor(w.Quu, w.Quf, a.lm, mu_lm, Lr, Lf, mu);
     } else {
 #pragma unroll
@@ -1206,13 +1206,16 @@ struct Solver {
             // (no barrier inside: the groups of a warp may run different T)
             if (bw) {
               const R eps = (R)a.eps;
+              // the next knot's record is loaded (16-byte vectors) while this one computes
+              R nr[RS];
+              if (g.lane < T) ld_vec<RS>(rec(traj, base, g.lane, cur), nr);
               for (int k = g.lane; k < T; k += G) {
-                const R* r = rec(traj, base, k, cur);
                 R x[n], u[m];
 #pragma unroll
-                for (int i = 0; i < n; ++i) x[i] = r[i];
+                for (int i = 0; i < n; ++i) x[i] = nr[i];
 #pragma unroll
-                for (int i = 0; i < m; ++i) u[i] = r[n + i];
+                for (int i = 0; i < m; ++i) u[i] = nr[n + i];
+                if (k + G < T) ld_vec<RS>(rec(traj, base, k + G, cur), nr);
                 R d[Sys::kDerivStride];
                 Sys::derivs_lane(P, x, u, eps, d, d + n * n, d + n * n + n * m, d + 2 * n * n + n * m,
                                  d + 2 * n * n + n * m + n, d + 2 * n * n + n * m + n + m * m);

@@ -99,7 +99,27 @@ def rigid_counts(params) -> dict:
     primal_sub = rnea + crba + N ** 3 // 3 + solve + 4 * N
     tangent_sub = 2 * rnea + solve + 4 * N
     return dict(N=N, n_sub=n_sub, primal=n_sub * primal_sub, tangent=n_sub * tangent_sub, costd=8 * N,
-                cost=6 * N)
+                cost=6 * N, rnea_sub=rnea)
+
+
+def derivative_flops_minimal(sys: int, n: int, m: int, params=None) -> int:
+    """A count of the derivative step that does not grow with the number of
+    tangent directions, for the rigid trees: per substep, the analytic
+    derivatives of inverse dynamics d ID / d(q, v) (Carpentier and Mansard,
+    RSS 2018: both N x N matrices in O(N d) spatial operations, taken here as
+    four Newton-Euler passes), M^-1 applied to their 2N columns and to the m
+    torque columns (2 N^2 each, the factor is the primal's), and the chain
+    rule through the substeps (the semi-implicit Euler step's Jacobian times
+    the accumulated n x (n + m) one: three N x N blocks times N x (n + m),
+    from the second substep on).  Other systems: as derivative_flops."""
+    if sys not in (ARM7, QUAD):
+        return derivative_flops(sys, n, m, params)
+    c = rigid_counts(params)
+    N, n_sub = c["N"], c["n_sub"]
+    rnea = c["rnea_sub"]
+    per_sub = 4 * rnea + (2 * N + m) * 2 * N * N + 4 * N
+    chain = 3 * 2 * N * N * (n + m)
+    return n_sub * per_sub + (n_sub - 1) * chain + c["costd"] + c["primal"]
 
 
 def derivative_flops(sys: int, n: int, m: int, params=None) -> int:
@@ -123,11 +143,13 @@ def rollout_flops(sys: int, n: int, m: int, params=None) -> int:
 
 def solve_flops(sys: int, n: int, m: int, T: np.ndarray, iters: np.ndarray, status: np.ndarray,
                 alpha_hist: np.ndarray, lanes_per_round: int, n_alpha: int, refine: bool, params=None,
-                actor: bool = False) -> float:
-    """Algorithmic FLOPs of one batched solve from its per-instance history."""
+                actor: bool = False, minimal_derivs: bool = False) -> float:
+    """Algorithmic FLOPs of one batched solve from its per-instance history
+    (minimal_derivs: the derivative step by derivative_flops_minimal)."""
     T = np.asarray(T, dtype=np.float64)
     iters = np.asarray(iters)
-    bwd = riccati_flops(n, m, refine) + derivative_flops(sys, n, m, params)
+    dflops = derivative_flops_minimal(sys, n, m, params) if minimal_derivs else derivative_flops(sys, n, m, params)
+    bwd = riccati_flops(n, m, refine) + dflops
     ro = rollout_flops(sys, n, m, params)
     total = float(np.sum(T) * (ro + (ACTOR_FLOPS_PER_KNOT if actor else 0)))   # warm-start rollout
     total += float(np.sum(T * iters) * bwd)             # one backward pass per iteration

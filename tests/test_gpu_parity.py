@@ -169,6 +169,15 @@ def test_pointmass_replay(P, oracle_mod, prec):
     _check_consistency(o, b, rg, prec)
 
 
+# Instances (of 24) whose replay is well conditioned by the oracle's own
+# sensitivity to a 1e-15 move of x0 (kappa < 1e-12 for FP64, < 1e-14 for
+# mixed), measured on the oracle for these seeds; kappa depends on the oracle
+# alone, so these are the number of instances each test holds to the strict
+# bounds.  The floors allow one instance less (the host's libm may round a
+# chaotic replay differently).
+PLANAR_WELL = {((20, 40), 5): (21, 5), ((20, 40), 60): (24, 15), ((20, 120), 20): (14, 6)}
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("T,iters", [((20, 40), 5), ((20, 40), 60), ((20, 120), 20)])
 def test_planar3_replay_ragged(P, oracle_mod, prec, T, iters):
@@ -179,7 +188,7 @@ def test_planar3_replay_ragged(P, oracle_mod, prec, T, iters):
     kappa = _sensitivity(o, b, ro, iters)
     rg = _replay(P, prob, b, ro, P.TO_FP64 if prec == "fp64" else P.TO_MIXED, iters, T_max=128)
     well = _check(ro, rg, kappa, prec, b.T)
-    assert well.mean() >= (0.4 if prec == "fp64" else 0.2)
+    assert well.sum() >= PLANAR_WELL[(T, iters)][0 if prec == "fp64" else 1] - 1, kappa
     _check_consistency(o, b, rg, prec, min_checked=b.x0.shape[0] // 4)
 
 
@@ -195,7 +204,7 @@ def test_planar3_replay_four_lanes(P, oracle_mod, prec):
     rg = _replay(P, prob, b, ro, P.TO_FP64 if prec == "fp64" else P.TO_MIXED, 20, T_max=128,
                  group_lanes=4, groups_per_block=16)
     well = _check(ro, rg, kappa, prec, b.T)
-    assert well.mean() >= (0.4 if prec == "fp64" else 0.2)
+    assert well.sum() >= PLANAR_WELL[((20, 120), 20)][0 if prec == "fp64" else 1] - 1, kappa
     _check_consistency(o, b, rg, prec, min_checked=b.x0.shape[0] // 4)
 
 
