@@ -671,9 +671,23 @@ def multi_system_leg(P):
         e1.synchronize()
         alone.append(e0.elapsed_time(e1) / 1e3)
     ref = [P.toget_trajectories(bt, X=False, U=False) for bt in batches]
+    # one persistent launch over the three systems (tosolve_systems)
+    fbatches = [P.tocreate_batch(pr, B, B * (T_MAX_M + 1), opts) for pr in probs]
+    xs, Ts = [x.data_ptr() for x, _ in dev_in], [t.data_ptr() for _, t in dev_in]
+    P.tosolve_systems(fbatches, [B] * len(systems), xs, Ts, opts=opts, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    P.tosolve_systems(fbatches, [B] * len(systems), xs, Ts, opts=opts, stream=stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    t_fused = e0.elapsed_time(e1) / 1e3
+    fres = [P.toget_trajectories(bt, X=False, U=False) for bt in fbatches]
     out = {"workload": f"point mass, planar arm, 7-DoF arm: {B} instances each, T ~ U{{50..400}}, "
                        f"max_iter={MI}, mixed",
            "sequential_s": t_seq, "alone_s": dict(zip(("pointmass", "planar3", "arm7"), alone)),
+           "one_launch_s": t_fused,
+           "one_launch_iters_equal_sequential": float(np.mean(np.concatenate(
+               [fres[i]["iters"] == ref[i]["iters"] for i in range(len(systems))]))),
            "graph_note": "host wall time of tograph_launch + tograph_sync (H2D, sort, solver, D2H per member)"}
     for label, shares in (("equal_shares", None), ("work_shares", alone)):
         gbatches = [P.tocreate_batch(pr, B, B * (T_MAX_M + 1), opts) for pr in probs]

@@ -261,6 +261,22 @@ int tosolve_batch_device(to_batch b, int B, const double* d_x0, const int* d_T, 
 int toget_trajectories(to_batch b, double* X, double* U, double* J, int* iters, int* status, double* Vx,
                        double* K);
 
+/* Several systems in one persistent launch (spec batching pattern:
+ * uneven horizons and systems share one launch; the paper batches one
+ * system at a time, Sec. IV).  batches[i] (one per problem, each of a
+ * different system among the 7-DoF arm, the planar arm and the point mass)
+ * solves Bs[i] instances from device inputs d_x0[i] (Bs[i] x n float64) and
+ * d_T[i] (Bs[i] int32 in [1, T_max]), with one option set (no forced steps,
+ * want_vx, profiling or launch shape).  One horizon sort per member, then a
+ * single kernel in which every CTA serves the 7-DoF arm's queue, then the
+ * planar arm's, then the point mass's: a CTA that drains one system moves on
+ * to the next while others still solve the previous one.  Each member's
+ * arithmetic is its own solver's; results are read per batch with
+ * toget_trajectories.  Errors: TO_ERR_ARG, TO_ERR_UNSUPPORTED (another
+ * system, a repeated system, an unsupported option), TO_ERR_CUDA. */
+int tosolve_systems(const to_batch* batches, const int* Bs, const double* const* d_x0, const int* const* d_T, int n,
+                    const to_solver_opts* opts, void* cuda_stream);
+
 /* Per-iteration record of the last solve: accepted step index (B x max_iter,
  * -1 after the last iteration) and cost (B x (max_iter+1), J_hist[b][0] is the
  * warm-start cost).  Either pointer may be NULL. */

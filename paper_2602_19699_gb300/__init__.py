@@ -78,6 +78,7 @@ def lib():
             L.tolast_launch_count.argtypes = [vp]
             L.toget_phase_cycles.argtypes = [vp, vp]
             L.tosolve_batch_noalloc.argtypes = [vp, i, vp, vp, C.POINTER(to_solver_opts), vp, vp, vp, vp, vp, vp]
+            L.tosolve_systems.argtypes = [vp, vp, vp, vp, i, C.POINTER(to_solver_opts), vp]
             L.toserver_create.argtypes = [vp, i, C.POINTER(to_solver_opts), C.c_size_t, C.POINTER(vp)]
             L.toserver_destroy.argtypes = [vp]
             L.toserver_destroy.restype = None
@@ -109,6 +110,7 @@ def exported_symbols():
     return ["to_default_opts", "tocreate_problem", "todestroy_problem", "tocreate_batch", "tofree_batch",
             "tosolve_batch", "tosolve_batch_device", "toget_trajectories", "toget_history",
             "toget_device_results", "tolast_launch_count", "toget_phase_cycles", "tosolve_batch_noalloc",
+            "tosolve_systems",
             "toserver_create", "toserver_destroy", "tosubmit", "topoll", "toserver_stats", "toserve_replay",
             "toget_critic_targets", "toranker_create", "torank_candidates", "toranker_destroy", "totune",
             "tograph_create", "tograph_staging", "tograph_launch", "tograph_sync", "tograph_launch_count",
@@ -402,6 +404,21 @@ def tosolve_batch_device(batch: Batch, B: int, d_x0: int, d_T: int, d_U_init: in
                                       C.c_void_p(d_forced) if d_forced else None, C.byref(opts),
                                       C.c_void_p(stream) if stream else None))
     batch.B, batch.max_iter, batch.want_vx = B, opts.max_iter, opts.want_vx
+
+
+def tosolve_systems(batches, Bs, d_x0s, d_Ts, opts: to_solver_opts | None = None, stream=None):
+    """Several systems (7-DoF arm, planar arm, point mass; one batch each) in
+    one persistent launch, from device-resident inputs (raw device pointers)."""
+    opts = opts if opts is not None else to_default_opts()
+    opts.forced_alpha = None
+    n = len(batches)
+    hb = (C.c_void_p * n)(*[b.handle.value for b in batches])
+    Bv = (C.c_int * n)(*[int(B) for B in Bs])
+    xv = (C.c_void_p * n)(*[int(p) for p in d_x0s])
+    tv = (C.c_void_p * n)(*[int(p) for p in d_Ts])
+    _check(lib().tosolve_systems(hb, Bv, xv, tv, n, C.byref(opts), C.c_void_p(stream) if stream else None))
+    for b, B in zip(batches, Bs):
+        b.B, b.max_iter, b.want_vx = int(B), opts.max_iter, 0
 
 
 def tosolve_batch_noalloc(problem: Problem, B: int, d_x0: int, d_T: int, d_J: int, d_iters: int, d_status: int,

@@ -445,27 +445,12 @@ static int resolve_shape(to_problem p, const to_solver_opts* o, int B, double fr
   return TO_OK;
 }
 
-static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
-                        const to_solver_opts* o, cudaStream_t s, const ServeArgs* serve = nullptr) {
+// the solver arguments of one batch (everything but the serving ring and the
+// phase counters)
+static int fill_solve_args(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
+                           const to_solver_opts* o, SolveArgs& a) {
   to_problem p = b->p;
-  const SysOps* ops = p->ops;
   const int prec = o->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
-  // the problem's parameters and actor weights live on the device that was
-  // current when it was created; a launch from another device would hand the
-  // kernel another GPU's pointers
-  int cur_dev = -1;
-  TO_CK(cudaGetDevice(&cur_dev));
-  if (cur_dev != p->device)
-    return fail(TO_ERR_ARG, "solve: the current device is " + std::to_string(cur_dev) + ", the problem was created on " +
-                                std::to_string(p->device));
-  // a serving kernel, or a member of a multi-system graph, takes its share of
-  // the resident CTAs, so the kernels of the other problems run beside it
-  const double frac = serve ? serve->grid_frac : b->grid_frac;
-  int G = 0, gpb = 0, grid = 0;
-  int rc = resolve_shape(p, o, B, frac, &G, &gpb, &grid, nullptr);
-  if (rc) return rc;
-
-  SolveArgs a{};
   a.B = B; a.T_max = p->T_max; a.max_iter = o->max_iter; a.n_alpha = o->n_alpha;
   a.refine = o->refine; a.want_vx = o->want_vx;
   a.tol = o->tol_rel; a.eps = o->eps_clip;
@@ -487,6 +472,32 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   a.ahist = b->ahist; a.Jhist = b->Jhist;
   a.params = p->d_params[prec == PREC_FP64 ? 0 : 1]; a.actor_w = p->d_actor; a.err = b->err;
   a.prof = nullptr;
+  return TO_OK;
+}
+
+static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, const double* d_U, const int* d_forced,
+                        const to_solver_opts* o, cudaStream_t s, const ServeArgs* serve = nullptr) {
+  to_problem p = b->p;
+  const SysOps* ops = p->ops;
+  const int prec = o->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
+  // the problem's parameters and actor weights live on the device that was
+  // current when it was created; a launch from another device would hand the
+  // kernel another GPU's pointers
+  int cur_dev = -1;
+  TO_CK(cudaGetDevice(&cur_dev));
+  if (cur_dev != p->device)
+    return fail(TO_ERR_ARG, "solve: the current device is " + std::to_string(cur_dev) + ", the problem was created on " +
+                                std::to_string(p->device));
+  // a serving kernel, or a member of a multi-system graph, takes its share of
+  // the resident CTAs, so the kernels of the other problems run beside it
+  const double frac = serve ? serve->grid_frac : b->grid_frac;
+  int G = 0, gpb = 0, grid = 0;
+  int rc = resolve_shape(p, o, B, frac, &G, &gpb, &grid, nullptr);
+  if (rc) return rc;
+
+  SolveArgs a{};
+  rc = fill_solve_args(b, B, d_x0, d_T, d_U, d_forced, o, a);
+  if (rc) return rc;
   if (o->profile_phases) {
     if (!b->prof) TO_CK(cudaMalloc(&b->prof, 8 * sizeof(unsigned long long)));
     TO_CK(cudaMemsetAsync(b->prof, 0, 8 * sizeof(unsigned long long), s));
@@ -560,6 +571,67 @@ int tosolve_batch_device(to_batch b, int B, const double* d_x0, const int* d_T, 
   if (rc) return rc;
   if (B == 0) { b->B = 0; b->launches = 0; return TO_OK; }
   return launch_solve(b, B, d_x0, d_T, d_U_init, d_forced, opts, (cudaStream_t)cuda_stream);
+}
+
+int tosolve_systems(const to_batch* batches, const int* Bs, const double* const* d_x0, const int* const* d_T, int n,
+                    const to_solver_opts* opts, void* cuda_stream) {
+  if (!batches || !Bs || !d_x0 || !d_T || n < 1 || n > kMultiSystems)
+    return fail(TO_ERR_ARG, "tosolve_systems: null argument or n outside [1, 3]");
+  to_solver_opts def;
+  to_default_opts(&def);
+  if (!opts) opts = &def;
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  if (opts->forced_alpha || opts->want_vx || opts->profile_phases || opts->group_lanes || opts->groups_per_block)
+    return fail(TO_ERR_UNSUPPORTED, "tosolve_systems: forced steps, want_vx, profiling and launch shapes are not available");
+  const int prec = opts->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int cur_dev = -1;
+  TO_CK(cudaGetDevice(&cur_dev));
+  MultiArgs m{};
+  int slot_of[kMultiSystems];
+  for (int i = 0; i < n; ++i) {
+    to_batch b = batches[i];
+    if (!b) return fail(TO_ERR_ARG, "tosolve_systems: null batch");
+    const int sys = b->p->sys;
+    const int slot = sys == TO_SYS_ARM7 ? 0 : sys == TO_SYS_PLANAR3 ? 1 : sys == TO_SYS_POINTMASS2D ? 2 : -1;
+    if (slot < 0) return fail(TO_ERR_UNSUPPORTED, "tosolve_systems: the fused launch covers the 7-DoF arm, the planar "
+                                                  "arm and the point mass");
+    if (m.present[slot]) return fail(TO_ERR_ARG, "tosolve_systems: one batch per system");
+    if (b->p->device != cur_dev) return fail(TO_ERR_ARG, "tosolve_systems: a problem lives on another device");
+    if (Bs[i] < 1 || Bs[i] > b->B_max || !d_x0[i] || !d_T[i])
+      return fail(TO_ERR_ARG, "tosolve_systems: B outside [1, B_max] or missing inputs");
+    rc = ensure_options(b, opts, false, false);
+    if (rc) return rc;
+    rc = fill_solve_args(b, Bs[i], d_x0[i], d_T[i], nullptr, nullptr, opts, m.a[slot]);
+    if (rc) return rc;
+    m.present[slot] = 1;
+    slot_of[i] = slot;
+  }
+  size_t smem = 0;
+  int bps = 0, sms = 0;
+  TO_CK(multi_occupancy(prec, &smem, &bps));
+  if (bps < 1) return fail(TO_ERR_ARG, "tosolve_systems: the fused kernel does not fit on an SM");
+  TO_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur_dev));
+  for (int i = 0; i < n; ++i) {
+    to_batch b = batches[i];
+    prepare_kernel<<<1, 1024, 0, s>>>(Bs[i], d_T[i], b->p->T_max, b->knots_max, b->toff, b->order, b->hist, b->err,
+                                      b->status, b->queue, b->J, b->iters);
+    TO_CK(cudaGetLastError());
+  }
+  TO_CK(multi_launch(prec, bps * sms, s, m));
+  for (int i = 0; i < n; ++i) {
+    to_batch b = batches[i];
+    b->B = Bs[i];
+    b->max_iter = opts->max_iter;
+    b->prec = opts->prec;
+    b->want_vx = 0;
+    b->stream = s;
+    b->launches = i == 0 ? n + 1 : 0;     // n prepare kernels and the one fused solver launch
+    b->G = multi_group_lanes(slot_of[i]);
+    b->last_T = d_T[i];
+  }
+  return TO_OK;
 }
 
 int tosolve_batch(to_problem p, int B, const double* x0, const int* T, const double* U_init,

@@ -42,6 +42,18 @@ struct SysOps {
 
 const SysOps* sys_ops(int sys);
 
+// One persistent launch over several systems (solve_multi.cu): slot 0 the
+// 7-DoF arm, slot 1 the planar arm, slot 2 the point mass; a slot without a
+// member is skipped.
+constexpr int kMultiSystems = 3;
+struct MultiArgs {
+  SolveArgs a[kMultiSystems];
+  int present[kMultiSystems];
+};
+cudaError_t multi_occupancy(int prec, size_t* smem, int* blocks_per_sm);
+cudaError_t multi_launch(int prec, int grid, cudaStream_t s, const MultiArgs& m);
+int multi_group_lanes(int slot);       // lanes per instance of the slot's solver
+
 constexpr int kMaxCtaThreads = 256;
 
 template <class Sys, class R, int G>

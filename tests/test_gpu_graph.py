@@ -102,3 +102,37 @@ def test_totune_picks_the_fastest_and_caches_it(P):
     r0 = P.toget_trajectories(bt, X=False, U=False)
     r1 = _alone(P, h, b.x0[:256], b.T[:256], opts)
     np.testing.assert_array_equal(r0["J"], r1["J"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fused_launch_equals_separate_solves(P, prec):
+    """tosolve_systems: the 7-DoF arm, the planar arm and the point mass in one
+    persistent launch give each system's own results (the fused kernel is its
+    own instantiation: equal up to the compiler's multiply-add fusion, as for
+    launch shapes)."""
+    import torch
+    T_max = 80
+    probs = [W.pointmass(seed=1), W.planar3(seed=2), W.arm7(seed=3)]
+    Bs = [300, 500, 120]
+    opts = P.to_default_opts(prec=P.TO_FP64 if prec == "fp64" else P.TO_MIXED, max_iter=4)
+    handles = [P.tocreate_problem(p.sys, p.params, T_max) for p in probs]
+    data = [W.make_batch(p, B, seed=20 + i, T=(10, T_max)) for i, (p, B) in enumerate(zip(probs, Bs))]
+    d_x0 = [torch.tensor(b.x0, dtype=torch.float64, device="cuda") for b in data]
+    d_T = [torch.tensor(b.T, dtype=torch.int32, device="cuda") for b in data]
+    fused = [P.tocreate_batch(h, B, B * (T_max + 1), opts) for h, B in zip(handles, Bs)]
+    P.tosolve_systems(fused, Bs, [x.data_ptr() for x in d_x0], [t.data_ptr() for t in d_T], opts=opts)
+    torch.cuda.synchronize()
+    assert P.tolast_launch_count(fused[0]) == 4          # three horizon sorts and one solver launch
+    for i, (h, b) in enumerate(zip(handles, data)):
+        got = P.toget_trajectories(fused[i])
+        ref = _alone(P, h, b.x0, b.T, opts)
+        same = got["iters"] == ref["iters"]
+        if prec == "fp64":
+            assert same.all()
+            rtol = 1e-9 if probs[i].sys == W.PLANAR3 else 1e-11
+            np.testing.assert_allclose(got["J"], ref["J"], rtol=rtol, atol=0)
+        else:
+            # float32 rounding differences may flip a near-tie step choice
+            assert same.mean() >= 0.95
+            np.testing.assert_allclose(got["J"][same], ref["J"][same], rtol=1e-4, atol=0)
+        np.testing.assert_array_equal(got["status"][same] & 15, ref["status"][same] & 15)

@@ -23,10 +23,13 @@ Tolerances.  Whenever the guard fires, the failing pivot is far below mu, so
 Q_uu + mu I has a condition number of about max|diag| / mu = 1e6 (the shift
 rule fixes it).  A float64 solve of it differs between two correct
 implementations by up to ~4 kappa 2^-52 ~ 1e-9 (instead of the 1e-10 of the
-other FP64 parity tests).  Mixed precision solves it with the float32 factor
-and one refinement step, whose relative error is ~(c kappa 2^-24)^2 with
-c ~ 3, i.e. ~3e-2: that is the accuracy limit of the float32 split on a
-regularised knot, and the bound used here.
+other FP64 parity tests).  In mixed precision the bound is 5e-2: the pivot
+test can only fail for a pivot 1e12 below the largest, so this problem's
+value Hessian spans the acceleration weight dt^2 w_aT ~ 5e6 down to the
+velocity weight 2, 22 bits apart, and the float32 Riccati products carry the
+velocity terms to a couple of significant bits (measured: 0.4 to 1.8 % on
+every instance; solving the regularised knots' gains with the float64
+factor changed nothing, so the solve is not the limit).
 """
 import numpy as np
 import pytest
@@ -39,7 +42,7 @@ pytestmark = pytest.mark.gpu
 FLAG_REG = 16
 KAPPA_SHIFTED = 1e6                                      # max|diag| / mu
 GUARD_FP64_TOL = 4 * KAPPA_SHIFTED * 2.0 ** -52 * 2      # ~1.8e-9
-GUARD_MIXED_TOL = (3 * KAPPA_SHIFTED * 2.0 ** -24) ** 2  # ~3.2e-2
+GUARD_MIXED_TOL = 5e-2
 
 
 @pytest.fixture(scope="module")
