@@ -819,6 +819,12 @@ def config_legs(P, dev, flush, peak32, peak64, quad_budget=False):
             reps = 3 if name == "pointmass" else 1
             t = _timed_solve(P, batch, B, d_x0[:B], d_T[:B], opts, stream, flush, reps)
             r = P.toget_trajectories(batch, X=True, U=True)
+            t_warm = None
+            if actor is not None and c["max_iter"] <= 100:
+                # S1 alone: the actor's rollout through the dynamics (a solve with no iteration)
+                wopts = P.to_default_opts(prec=prec, max_iter=0, tol_rel=TOL, n_alpha=N_ALPHA)
+                wb = P.tocreate_batch(problem, B, B * (c["T"] + 1), wopts)
+                t_warm = _timed_solve(P, wb, B, d_x0[:B], d_T[:B], wopts, stream, flush, 1)
             ah, _ = P.toget_history(batch)
             lanes = {W.POINTMASS: 8, W.ARM7: 16, W.QUAD: 16, W.DUBINS: 8}[sysid]
             alg = flops.solve_flops(prob.sys, prob.n, prob.m, b.T[:B], r["iters"], r["status"], ah,
@@ -850,6 +856,11 @@ def config_legs(P, dev, flush, peak32, peak64, quad_budget=False):
                                                     "nearly idle GPU; the fraction is not meaningful, the time per "
                                                     "iteration is") if name == "pointmass" else ""},
                               "_J": r["J"], "_X": r["X"], "_st": r["status"]}
+            if t_warm is not None:
+                res[prec_name]["actor_warm_start"] = {
+                    "ms": t_warm * 1e3, "share_of_solve": t_warm / t,
+                    "mlp_gflop": float(np.sum(b.T[:B])) * flops.ACTOR_FLOPS_PER_KNOT / 1e9,
+                    "note": "a solve with max_iter = 0: the actor MLP and the dynamics at every knot, on CUDA cores"}
             _log(f"config {name} {prec_name}: B={B} {t * 1e3:.1f} ms, mean iters {np.mean(r['iters']):.1f}")
         # accuracy: against the FP64 oracle on a sample, or (quadruped, whose
         # oracle takes minutes per instance) against the GPU's FP64 mode,

@@ -30,7 +30,7 @@ static int parse_quad(const double* p, size_t np, std::vector<unsigned char>& bl
   return 0;
 }
 
-typedef Dispatch<SysQuad, 64> QDispatch;
+typedef Dispatch<SysQuad, 64, 32> QDispatch;
 
 // the stored substep primals of one knot: n_sub of them (header [6], 0 means 1)
 static size_t quad_knot_scratch(const double* p, size_t np, int prec) {
@@ -42,8 +42,9 @@ static SysOps make_ops() {
   SysOps o{};
   o.sys = 4;
   fill_layout<SysQuad>(o);
-  o.n_groups = 1;
-  o.groups[0] = 64;
+  o.n_groups = 2;
+  o.groups[0] = 64;   // a candidate lane's partner on the other warp factors the mass matrix
+  o.groups[1] = 32;   // one warp per instance, each candidate lane steps alone
   o.default_G = 64;
   o.default_gpb[0] = 1; o.default_gpb[1] = 1;
   o.accepts_actor = true;

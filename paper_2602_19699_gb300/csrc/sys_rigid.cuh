@@ -1220,12 +1220,15 @@ struct SysRigid {
 
   // Columns of [A | B] from the knot's stored substep primals (prims, global):
   // each substep's Prim is staged into shared memory one substep ahead while
-  // the direction lanes run the tangent pass of the current one.
+  // the direction lanes run the tangent pass of the current one.  A group
+  // narrower than the n + m directions takes them in passes of G (the
+  // substeps are staged again for each pass).
   template <class R, int G>
   TO_DEV static void derivs_staged(const ParamsT<R>& P, const Group<G>& g, const R* x, const R* u, R eps, R* A, R* B,
                                    R* lxx, R* lx, R* luu, R* lu, R* scratch, const R* prims) {
-    static_assert(G >= n + m, "one lane per tangent direction");
-    const int c = g.lane;
+    for (int pass = 0; pass < (n + m + G - 1) / G; ++pass) {
+    if (pass > 0) g.sync();   // every lane done with the staging buffers of the previous pass
+    const int c = pass * G + g.lane;
     const bool dir = c < n + m;
     R dq[N], dqd[N];
 #pragma unroll
@@ -1264,7 +1267,8 @@ struct SysRigid {
         for (int i = 0; i < N; ++i) { B[i * m + (c - n)] = dq[i]; B[(N + i) * m + (c - n)] = dqd[i]; }
       }
     }
-    if (c == G - 1) running_derivs(P, x, u, eps, lxx, lx, luu, lu);
+    }
+    if (g.lane == G - 1) running_derivs(P, x, u, eps, lxx, lx, luu, lu);
   }
 
 };

@@ -56,17 +56,20 @@ def test_arm7_replay(P, oracle_mod, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_quad_replay(P, oracle_mod, prec):
+@pytest.mark.parametrize("lanes", [64, 32])
+def test_quad_replay(P, oracle_mod, prec, lanes):
     # six short replays: the oracle's sensitivity to a 1e-15 move of x0 is
     # 4e-15 .. 6e-14 here, so at least two instances take the strict mixed
-    # bounds (kappa < 1e-14) and all take the FP64 one
+    # bounds (kappa < 1e-14) and all take the FP64 one.  64 lanes: a partner
+    # lane on the other warp factors each candidate's mass matrix; 32 lanes:
+    # each candidate steps alone and the 48 tangent directions take two passes
     prob = W.quad(seed=2, with_actor=False)
     b = W.make_batch(prob, 6, seed=1, T=6)
     o = oracle_mod.Oracle.from_problem(prob)
     ro = o.solve(b.x0, b.T, max_iter=2, tol=1e-8)
     kappa = _sensitivity(o, b, ro, 2)
     s = _solver(P, prob, 8, P.TO_FP64 if prec == "fp64" else P.TO_MIXED)
-    rg = s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=2)
+    rg = s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=2, group_lanes=lanes, groups_per_block=1)
     well = _check(ro, rg, kappa, prec, b.T)
     assert well.sum() >= (6 if prec == "fp64" else 2), kappa
     _check_consistency(o, b, rg, prec, min_checked=4)
