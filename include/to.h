@@ -395,7 +395,12 @@ int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_
  * opts->prec: later solves that leave both at 0 use it.  rows (may be NULL)
  * receives up to max_rows measured shapes; *n_rows how many were measured.
  * The calibration batch should fill the GPU (several instances per SM) so
- * the choice holds for large batches.  Errors: TO_ERR_ARG, TO_ERR_CUDA.
+ * the choice holds for large batches.  With the environment variable
+ * TO_TUNE_CACHE naming a file, the choice is also appended to that file and
+ * a later call with the same key (system, sizes, T_max, batch size and mean
+ * horizon in powers of two, precision, LM mode, GPU name and SM count, the
+ * library's build time) takes it from there without timing: *n_rows is then
+ * 1 and rows[0] the stored shape.  Errors: TO_ERR_ARG, TO_ERR_CUDA.
  */
 typedef struct {
   int group_lanes, groups_per_block;

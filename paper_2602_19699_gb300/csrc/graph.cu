@@ -4,6 +4,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -33,6 +36,61 @@ struct TuneScratch {
   }
 };
 
+// The persisted choice of the autotuner: when the environment variable
+// TO_TUNE_CACHE names a file, each tuned shape is appended to it as one line
+//   <key> <group_lanes> <groups_per_block> <ms>
+// and a later totune with the same key (in any process) takes the shape from
+// the file instead of timing again.  The key holds what the best shape
+// depends on: the system and its sizes, T_max, the batch size and the mean
+// horizon (powers of two), the precision and LM mode, the GPU's name and SM
+// count, and the library's build time (a rebuilt kernel is tuned again).
+std::string tune_key(to_problem p, int B, const int* T, const to_solver_opts* o) {
+  long long sum = 0;
+  for (int i = 0; i < B; ++i) sum += T[i];
+  const int meanT = (int)(sum / std::max(B, 1));
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "";
+  std::string name(prop.name);
+  for (char& c : name) if (c == ' ' || c == '\t') c = '_';
+  auto log2i = [](long long v) { int l = 0; while (v > 1) { v >>= 1; ++l; } return l; };
+  char buf[512];
+  snprintf(buf, sizeof buf, "sys%d_n%d_m%d_Tmax%d_B2^%d_T2^%d_prec%d_reg%d_%s_sm%d_build%s_%s", p->sys, p->n, p->m,
+           p->T_max, log2i(B), log2i(meanT), o->prec, o->reg, name.c_str(), prop.multiProcessorCount, __DATE__, __TIME__);
+  std::string key(buf);
+  for (char& c : key) if (c == ' ') c = '_';
+  return key;
+}
+
+bool tune_cache_lookup(const std::string& key, int* G, int* gpb, double* ms) {
+  const char* path = std::getenv("TO_TUNE_CACHE");
+  if (!path || !*path || key.empty()) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    char k[600];
+    int g = 0, b = 0;
+    double t = 0;
+    if (std::sscanf(line, "%599s %d %d %lf", k, &g, &b, &t) == 4 && key == k) {
+      *G = g; *gpb = b; *ms = t;          // the last entry for a key wins
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void tune_cache_store(const std::string& key, int G, int gpb, double ms) {
+  const char* path = std::getenv("TO_TUNE_CACHE");
+  if (!path || !*path || key.empty()) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %.6f\n", key.c_str(), G, gpb, ms);
+  std::fclose(f);
+}
+
 }  // namespace
 
 int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* opts, to_tune_row* rows,
@@ -47,6 +105,27 @@ int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* 
   for (int i = 0; i < B; ++i) {
     if (T[i] < 1 || T[i] > p->T_max) return to_fail(TO_ERR_ARG, "totune: horizon outside [1, T_max]");
     knots += (long long)T[i] + 1;
+  }
+  const int prec0 = opts->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
+  const std::string key = tune_key(p, B, T, opts);
+  {
+    int G = 0, gpb = 0;
+    double ms = 0;
+    if (tune_cache_lookup(key, &G, &gpb, &ms)) {
+      to_solver_opts o = *opts;
+      o.group_lanes = G;
+      o.groups_per_block = gpb;
+      int g2 = 0, b2 = 0, grid = 0, bps = 0;
+      if (to_resolve_shape(p, &o, B, 1.0, &g2, &b2, &grid, &bps) == TO_OK) {
+        opts->group_lanes = G;
+        opts->groups_per_block = gpb;
+        p->tuned_G[prec0] = G;
+        p->tuned_gpb[prec0] = gpb;
+        if (rows && max_rows > 0) rows[0] = to_tune_row{G, gpb, grid, bps, ms};
+        if (n_rows) *n_rows = max_rows > 0 ? 1 : 0;
+        return TO_OK;
+      }
+    }
   }
   TuneScratch w;
   to_solver_opts base = *opts;
@@ -98,6 +177,7 @@ int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* 
     }
   }
   if (!best_G) return to_fail(TO_ERR_ARG, "totune: no launch shape fits an SM");
+  tune_cache_store(key, best_G, best_gpb, best_ms);
   opts->group_lanes = best_G;
   opts->groups_per_block = best_gpb;
   p->tuned_G[prec] = best_G;

@@ -136,3 +136,29 @@ def test_fused_launch_equals_separate_solves(P, prec):
             assert same.mean() >= 0.95
             np.testing.assert_allclose(got["J"][same], ref["J"][same], rtol=1e-4, atol=0)
         np.testing.assert_array_equal(got["status"][same] & 15, ref["status"][same] & 15)
+
+
+def test_totune_persisted_choice(P, tmp_path, monkeypatch):
+    """With TO_TUNE_CACHE set, the tuned shape is written to the file and a
+    later call with the same workload reads it back without timing."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("TO_TUNE_CACHE", str(cache))
+    prob = W.pointmass(seed=8)
+    b = W.make_batch(prob, 1024, seed=9, T=(20, 50))
+    h = P.tocreate_problem(prob.sys, prob.params, 50)
+    opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=3)
+    rows = P.totune(h, b.x0, b.T, opts)
+    assert len(rows) >= 4
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].split()[1:3] == [str(opts.group_lanes), str(opts.groups_per_block)]
+    # a new problem handle, the same workload: the stored shape, no timing
+    h2 = P.tocreate_problem(prob.sys, prob.params, 50)
+    opts2 = P.to_default_opts(prec=P.TO_MIXED, max_iter=3)
+    rows2 = P.totune(h2, b.x0, b.T, opts2)
+    assert len(rows2) == 1
+    assert (opts2.group_lanes, opts2.groups_per_block) == (opts.group_lanes, opts.groups_per_block)
+    assert len(cache.read_text().splitlines()) == 1
+    # another precision is another key
+    opts3 = P.to_default_opts(prec=P.TO_FP64, max_iter=3)
+    assert len(P.totune(h2, b.x0, b.T, opts3)) >= 4
+    assert len(cache.read_text().splitlines()) == 2
