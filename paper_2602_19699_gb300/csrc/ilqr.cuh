@@ -357,7 +357,7 @@ struct Solver {
             r[i] = (float)t;
           }
         } else {
-          const float muf = d2f(mu);
+          const float muf = (float)mu;
 #pragma unroll
           for (int i = 0; i < m; ++i) {
             Acc<float> t;
@@ -404,17 +404,6 @@ struct Solver {
     const int rb = (int)((__fsqrt_rn((float)(8 * eb + 1)) - 1.0f) * 0.5f);   // row counted from the bottom
     i = n - 1 - rb;
     j = n - 1 - (eb - rb * (rb + 1) / 2);
-  }
-
-  // float32 <-> float64 of the solver's own values without the float64 pipe
-  // in mixed mode (plain casts in float64 mode, where they are no-ops)
-  TO_DEV static double to_f64(R x) {
-    if constexpr (sizeof(R) == 4) return f2d(x);
-    else return (double)x;
-  }
-  TO_DEV static R to_R(double x) {
-    if constexpr (sizeof(R) == 4) return d2f(x);
-    else return (R)x;
   }
 
   // the same for small n on the integer pipe: walk the rows (no square root)
@@ -505,7 +494,7 @@ struct Solver {
 #pragma unroll
         for (int r = 0; r < n; ++r) t += w.Bm[r * m + i] * vb[r];
         if (st) {
-          w.Quu[i * m + c] = to_f64(t);
+          w.Quu[i * m + c] = (double)t;
           w.Quf[i * m + c] = t;
         }
       }
@@ -530,7 +519,7 @@ struct Solver {
       for (int i = 0; i < m; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j) Q[i * m + j] = w.Quu[i * m + j];
-      const double mx = to_f64(mxr);
+      const double mx = (double)mxr;
       auto cols = [&]() {
 #pragma unroll
         for (int s = 0; s < (n + G - 1) / G; ++s) {
@@ -586,7 +575,7 @@ struct Solver {
 #pragma unroll
       for (int i = 0; i < m; ++i)
 #pragma unroll
-        for (int j = 0; j <= i; ++j) Lf[i * m + j] = to_R(Lr[i * m + j]);
+        for (int j = 0; j <= i; ++j) Lf[i * m + j] = (R)Lr[i * m + j];
     }
     g.sync();
     // 3. gain columns (c < n: K[:, c]; c == n: k)
