@@ -325,7 +325,7 @@ def run_gb300(args):
     ah, _ = P.toget_history(batch)
     alg = flops.solve_flops(prob.sys, prob.n, prob.m, b.T, J_g["iters"], J_g["status"], ah,
                             lanes_per_round=min(opts.group_lanes, 16), n_alpha=N_ALPHA, refine=True)
-    alg64 = flops.solve_flops_fp64(prob.m, b.T, J_g["iters"], J_g["status"])
+    alg64 = flops.solve_flops_fp64(prob.m, b.T, J_g["iters"], J_g["status"], group_lanes=opts.group_lanes)
 
     # ---- e2e: the public graph API.  Each step writes the inputs into the
     # graph's pinned staging and replays the captured solve: host-to-device
@@ -490,7 +490,8 @@ def run_gb300(args):
     multi = None if args.no_extras else multi_system_leg(P)
     achieved = alg / (t_local / args.steps) / 1e12
     # the binding roofline of the mixed solve: its float32 work at the FP32
-    # peak plus its float64 work (the Q_uu Cholesky) at the FP64 peak
+    # peak plus its float64 work (the Q_uu Cholesky where it runs in float64)
+    # at the FP64 peak
     peak_mix = flops.effective_peak(alg - alg64, alg64, peak32, peak64)
     traffic = measured_traffic()
     n = ws
@@ -508,8 +509,9 @@ def run_gb300(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "precision": "mixed: f32 rollouts/derivatives/Riccati products; f64 Q_uu Cholesky, pivot test, "
-                     "refinement residual, cost comparison",
+        "precision": "mixed: f32 rollouts, derivatives, Riccati products and Q_uu Cholesky; f64 Cholesky with "
+                     "the pivot guard for a Q_uu with a pivot below 2^-10 of its largest diagonal entry; "
+                     "float-float gain refinement residual, compensated state and cost sums; f64 cost comparison",
         "data": "synthetic (seeded generator)",
         "config": {
             "workload": f"planar3 arm, B={B} per GPU, T~U{{{T_RANGE[0]}..{T_RANGE[1]}}}, zero warm start, "
@@ -537,7 +539,7 @@ def run_gb300(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_mix, "unit": "TFLOP/s",
                      "frac": achieved / peak_mix, "traffic": traffic,
                      "peak_source": f"derived: float32 work at {peak32:.1f} TFLOP/s ({sms} SMs x 128 FP32 lanes x 2 x "
-                                    f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz) plus float64 work (Q_uu Cholesky, "
+                                    f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz) plus float64 work (Q_uu Cholesky where it runs in float64, "
                                     f"{alg64 / alg * 100:.2f} % of the FLOPs) at {peak64:.2f} TFLOP/s (1/64 rate); "
                                     f"max SM clock from {pk_src} peaks",
                      "frac_of_fp32_peak": achieved / peak32,
@@ -755,6 +757,10 @@ def bic_leg(P, peak32):
 # the full batch for 20 iterations (throughput and accuracy against the
 # oracle's stored 20-iteration solve of 8 instances).  "quad_budget" takes
 # about 140 s and runs only with --quad-budget.
+# lanes per instance of each system's default launch shape, by system id
+# (point mass 1, planar arm 2, 7-DoF arm 3, quadruped 4, Dubins car 5)
+SYS_LANES = {1: 8, 2: 8, 3: 32, 4: 64, 5: 8}
+
 CONFIGS = {
     "pointmass": dict(sys="pointmass", B=64, T=50, max_iter=100, precs=("fp64",), oracle_sample=64, fp64_subset=None),
     "arm7": dict(sys="arm7", B=16384, T=200, max_iter=288, precs=("mixed", "fp64"), oracle_sample=64,
@@ -826,7 +832,7 @@ def config_legs(P, dev, flush, peak32, peak64, quad_budget=False):
                 wb = P.tocreate_batch(problem, B, B * (c["T"] + 1), wopts)
                 t_warm = _timed_solve(P, wb, B, d_x0[:B], d_T[:B], wopts, stream, flush, 1)
             ah, _ = P.toget_history(batch)
-            lanes = {W.POINTMASS: 8, W.ARM7: 16, W.QUAD: 16, W.DUBINS: 8}[sysid]
+            lanes = {W.POINTMASS: 8, W.ARM7: 16, W.QUAD: 16, W.DUBINS: 8}[sysid]   # step sizes per round
             alg = flops.solve_flops(prob.sys, prob.n, prob.m, b.T[:B], r["iters"], r["status"], ah,
                                     lanes_per_round=lanes, n_alpha=N_ALPHA, refine=prec == P.TO_MIXED,
                                     params=prob.params, actor=actor is not None)
@@ -834,7 +840,8 @@ def config_legs(P, dev, flush, peak32, peak64, quad_budget=False):
                                         lanes_per_round=lanes, n_alpha=N_ALPHA, refine=prec == P.TO_MIXED,
                                         params=prob.params, actor=actor is not None, minimal_derivs=True)
             if prec == P.TO_MIXED:
-                alg64 = flops.solve_flops_fp64(prob.m, b.T[:B], r["iters"], r["status"])
+                alg64 = flops.solve_flops_fp64(prob.m, b.T[:B], r["iters"], r["status"],
+                                               group_lanes=SYS_LANES[sysid])
                 peak = flops.effective_peak(alg - alg64, alg64, peak32, peak64)
                 peak_min = flops.effective_peak(alg_min - alg64, alg64, peak32, peak64)
             else:
@@ -850,7 +857,8 @@ def config_legs(P, dev, flush, peak32, peak64, quad_budget=False):
                                            "algorithmic_flops_minimal_derivatives": alg_min,
                                            "frac_minimal_derivatives": alg_min / t / 1e12 / peak_min,
                                            "peak_source": ("derived: float32 work at the FP32 peak plus the Q_uu "
-                                                           "Cholesky at the FP64 peak" if prec == P.TO_MIXED else
+                                                           "Cholesky, where it runs in float64, at the FP64 peak"
+                                                           if prec == P.TO_MIXED else
                                                            "derived FP64 ALU rate at the max SM clock"),
                                            "note": ("64 instances of 50 knots: a dependent chain per instance on a "
                                                     "nearly idle GPU; the fraction is not meaningful, the time per "

@@ -57,10 +57,13 @@ enum {
 /* arithmetic of the solve */
 enum {
   TO_FP64 = 0, /* every step in float64                                        */
-  TO_MIXED = 1 /* float32 rollouts, derivatives and Riccati products; float64
-                  Q_uu Cholesky, pivot test and line-search cost comparison;
-                  the refinement residual of the gain solve and the cost
-                  accumulation are float-float (about 48 significant bits)    */
+  TO_MIXED = 1 /* float32 rollouts, derivatives and Riccati products; the
+                  Q_uu Cholesky in float32 when every pivot exceeds 2^-10 of
+                  the largest diagonal entry (groups of 2 to 31 lanes,
+                  clipped Hessians), else in float64 with the pivot test;
+                  float64 line-search cost comparison; the refinement
+                  residual of the gain solve and the cost accumulation are
+                  float-float (about 48 significant bits)                     */
 };
 
 /* return codes */
@@ -308,6 +311,30 @@ int toget_phase_cycles(to_batch b, unsigned long long* out);
 
 /* Number of kernels the last tosolve_batch / tosolve_batch_device launched. */
 int tolast_launch_count(to_batch b);
+
+/* Bounds-checked build.  The library built with -DTO_CHECKED (nvcc_build
+ * checked=True: _lib/libto_checked.so; the Python binding loads it when the
+ * environment sets TO_CHECKED=1) checks every computed index of the solver
+ * kernel against the buffer it addresses: the instance index against the
+ * batch (or the server's seats), the horizon against [1, T_max], every knot
+ * record, gain record, V_x row and derivative-scratch row against the
+ * batch's knot capacity, the trajectory slot against the line-search width,
+ * and the iteration index of the step-size history, the forced sequence and
+ * the caller's warm start against their sizes.  A violation is recorded per
+ * problem and the access goes to the buffer's first element instead; the
+ * solve's results are then meaningless, but nothing is read or written
+ * outside an allocation.  The release build compiles the checks away.
+ *
+ * tobounds_checked: 1 in the checked build, 0 in the release build.
+ * toget_bounds_report: after synchronising the device, out4 receives the
+ * problem's report since its creation (or the last reset): [0] the number of
+ * violations, [1] the first one's site (1 instance index, 2 serving seat,
+ * 3 horizon, 4 knot record, 5 trajectory slot, 6 gain record, 7 V_x row,
+ * 8 derivative scratch, 9 forced step, 10 warm start, 11 history), [2] its
+ * index, [3] the limit it broke.  reset != 0 zeroes the report afterwards.
+ * TO_ERR_UNSUPPORTED in the release build. */
+int tobounds_checked(void);
+int toget_bounds_report(to_problem p, long long* out4, int reset);
 
 /*
  * Serving: continuous batching of single OCP requests (the paper's real-time

@@ -7,6 +7,10 @@ fallback: calling into the library without a built ``libto.so`` or without a
 CUDA device raises.
 
 ``Solver`` is a small convenience wrapper (one problem + one reusable batch).
+
+With the environment variable ``TO_CHECKED=1`` the binding loads the
+bounds-checked build ``_lib/libto_checked.so`` (``build(checked=True)``)
+instead of the release library.
 """
 from __future__ import annotations
 
@@ -17,7 +21,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libto.so")
+CHECKED = os.environ.get("TO_CHECKED", "0") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "_lib", "libto_checked.so" if CHECKED else "libto.so")
 
 TO_SYS_POINTMASS2D, TO_SYS_PLANAR3, TO_SYS_ARM7, TO_SYS_QUAD18, TO_SYS_DUBINS = 1, 2, 3, 4, 5
 TO_FP64, TO_MIXED = 0, 1
@@ -50,9 +55,9 @@ _lib = None
 _lock = threading.Lock()
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, checked: bool = CHECKED) -> str:
     from . import nvcc_build as _b
-    return _b.build(force=force)
+    return _b.build(force=force, checked=checked)
 
 
 def lib():
@@ -61,7 +66,8 @@ def lib():
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"libto.so is not built ({LIB_PATH}); run paper_2602_19699_gb300.build()")
+                raise RuntimeError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); "
+                                   f"run paper_2602_19699_gb300.build({'checked=True' if CHECKED else ''})")
             L = C.CDLL(LIB_PATH)
             vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
             L.tocreate_problem.argtypes = [C.POINTER(to_problem_desc), C.POINTER(vp)]
@@ -77,6 +83,8 @@ def lib():
             L.toget_device_results.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
             L.tolast_launch_count.argtypes = [vp]
             L.toget_phase_cycles.argtypes = [vp, vp]
+            L.tobounds_checked.argtypes = []
+            L.toget_bounds_report.argtypes = [vp, vp, i]
             L.tosolve_batch_noalloc.argtypes = [vp, i, vp, vp, C.POINTER(to_solver_opts), vp, vp, vp, vp, vp, vp]
             L.tosolve_systems.argtypes = [vp, vp, vp, vp, i, C.POINTER(to_solver_opts), vp]
             L.toserver_create.argtypes = [vp, i, C.POINTER(to_solver_opts), C.c_size_t, C.POINTER(vp)]
@@ -114,7 +122,7 @@ def exported_symbols():
             "toserver_create", "toserver_destroy", "tosubmit", "topoll", "toserver_stats", "toserve_replay",
             "toget_critic_targets", "toranker_create", "torank_candidates", "toranker_destroy", "totune",
             "tograph_create", "tograph_staging", "tograph_launch", "tograph_sync", "tograph_launch_count",
-            "tograph_destroy", "tolast_error"]
+            "tograph_destroy", "tolast_error", "tobounds_checked", "toget_bounds_report"]
 
 
 class Ranker:
@@ -481,6 +489,18 @@ def toget_phase_cycles(batch: Batch) -> dict:
     d = {k: int(v) for k, v in zip(PHASES, out[:7])}
     d["total"] = int(out[7])
     return d
+
+
+def tobounds_checked() -> bool:
+    return bool(lib().tobounds_checked())
+
+
+def toget_bounds_report(problem, reset: bool = False) -> dict:
+    """The problem's bounds-check report (checked build only; raises
+    ToError TO_ERR_UNSUPPORTED in the release build)."""
+    out = np.zeros(4, np.int64)
+    _check(lib().toget_bounds_report(problem.handle, _ptr(out), int(reset)))
+    return {"violations": int(out[0]), "site": int(out[1]), "index": int(out[2]), "limit": int(out[3])}
 
 
 def tolast_launch_count(batch: Batch) -> int:

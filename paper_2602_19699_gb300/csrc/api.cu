@@ -247,6 +247,10 @@ int tocreate_problem(const to_problem_desc* d, to_problem* out) {
   if (e == cudaSuccess) e = cudaMemcpy(p->d_params[0], blob64.data(), blob64.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_params[1], blob32.size());
   if (e == cudaSuccess) e = cudaMemcpy(p->d_params[1], blob32.data(), blob32.size(), cudaMemcpyHostToDevice);
+#ifdef TO_CHECKED
+  if (e == cudaSuccess) e = cudaMalloc(&p->chk, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(p->chk, 0, 4 * sizeof(unsigned long long));
+#endif
   if (e == cudaSuccess && d->actor_w) {
     // W1 b1 W2 b2 W3 b3 with every W (out x in, row-major) stored transposed
     const int H = 256, n = d->n, m = d->m;
@@ -280,11 +284,31 @@ int tocreate_problem(const to_problem_desc* d, to_problem* out) {
   return TO_OK;
 }
 
+int tobounds_checked(void) {
+#ifdef TO_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int toget_bounds_report(to_problem p, long long* out4, int reset) {
+  if (!p || !out4) return fail(TO_ERR_ARG, "toget_bounds_report: null argument");
+  if (!p->chk) return fail(TO_ERR_UNSUPPORTED, "toget_bounds_report: the library was built without bounds checks");
+  unsigned long long h[4];
+  TO_CK(cudaDeviceSynchronize());
+  TO_CK(cudaMemcpy(h, p->chk, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 4; ++i) out4[i] = (long long)h[i];
+  if (reset) TO_CK(cudaMemset(p->chk, 0, sizeof(h)));
+  return TO_OK;
+}
+
 void todestroy_problem(to_problem p) {
   if (!p) return;
   for (void* q : p->d_params)
     if (q) cudaFree(q);
   if (p->d_actor) cudaFree(p->d_actor);
+  if (p->chk) cudaFree(p->chk);
   delete p;
 }
 
@@ -472,6 +496,8 @@ static int fill_solve_args(to_batch b, int B, const double* d_x0, const int* d_T
   a.ahist = b->ahist; a.Jhist = b->Jhist;
   a.params = p->d_params[prec == PREC_FP64 ? 0 : 1]; a.actor_w = p->d_actor; a.err = b->err;
   a.prof = nullptr;
+  a.knots_cap = b->knots_max;
+  a.chk = p->chk;
   return TO_OK;
 }
 

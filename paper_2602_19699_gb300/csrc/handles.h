@@ -19,6 +19,7 @@ struct to_problem_s {
   size_t knot_scratch[2] = {0, 0};   // per-knot derivative scratch elements (FP64, mixed); 0 = none
   int tuned_G[2] = {0, 0};     // autotuned launch shape per precision (FP64, mixed); 0 = none
   int tuned_gpb[2] = {0, 0};
+  unsigned long long* chk = nullptr;   // bounds-check report of the checked build (4 words), else null
 };
 
 struct to_batch_s {

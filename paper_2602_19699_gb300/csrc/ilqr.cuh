@@ -31,6 +31,7 @@
 // float64 (refine = 2); the cost is accumulated as a compensated float32 pair
 // (about 48 significant bits) and compared in float64.
 #pragma once
+#include <cfloat>
 #include <type_traits>
 
 #include "common.cuh"
@@ -96,6 +97,35 @@ struct SolveArgs {
   long long kscr;           // its elements per knot
   const int* err;           // set by the prepare kernel on malformed input
   unsigned long long* prof; // 8 per-phase cycle counters, or null (tracing off)
+  long long knots_cap;      // knot records the buffers hold (traj, gains, vx, dscr)
+  unsigned long long* chk;  // bounds-check report (checked build), or null
+};
+
+// Bounds checks of the checked build (compiled with TO_CHECKED).  An index
+// outside [0, lim) is recorded in a.chk -- [0] the number of violations,
+// [1] the first one's site, [2] its index, [3] its limit -- and replaced by
+// 0, so the access lands on the buffer's first element instead of outside
+// the buffer.  In the release build both helpers compile to nothing.
+#ifdef TO_CHECKED
+TO_DEV bool ck_ok(const SolveArgs& a, long long i, long long lim, int site) {
+  if (i >= 0 && i < lim) return true;
+  if (a.chk && atomicAdd(a.chk, 1ull) == 0ull) {
+    a.chk[1] = (unsigned long long)site;
+    a.chk[2] = (unsigned long long)i;
+    a.chk[3] = (unsigned long long)lim;
+  }
+  return false;
+}
+#else
+TO_DEV constexpr bool ck_ok(const SolveArgs&, long long, long long, int) { return true; }
+#endif
+TO_DEV long long ck(const SolveArgs& a, long long i, long long lim, int site) {
+  return ck_ok(a, i, lim, site) ? i : 0;
+}
+// check sites (the report's [1])
+enum {
+  CK_ORDER = 1, CK_SEAT, CK_HORIZON, CK_RECORD, CK_SLOT, CK_GAINS, CK_VX, CK_DSCR, CK_FORCED, CK_UINIT,
+  CK_HIST
 };
 
 // per-phase clock64 accounting (tracing); one timer thread per warp / CTA
@@ -454,11 +484,41 @@ struct Solver {
     return ok;
   }
 
+  // The factor of Q_uu in float32 (reciprocal pivots on the diagonal), from
+  // the float32 Q_uu; true when every pivot exceeds 2^-10 of the largest
+  // diagonal magnitude (and FLT_MIN).  The float32 pivots are those of Q_uu
+  // + dQ with |dQ| <= (m + 1) 2^-24 max|diag| entrywise (Higham 2002,
+  // Thm. 10.3), so a pivot at the threshold is ~2^14 / (m + 1) times that
+  // perturbation, and nine orders of magnitude above the float64 test's
+  // 1e-12; a NaN or infinite entry reaches a pivot and fails the test.
+  TO_DEV static bool chol_f32(const R* Q, R mxr, float (&L)[m * m]) {
+    const float tau = fmaxf(0x1p-10f * (float)mxr, FLT_MIN);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < m; ++j) {
+      float s = (float)Q[j * m + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= L[j * m + k] * L[j * m + k];
+      ok = ok & (s > tau);
+      const float r = rsqrtf(s);
+      L[j * m + j] = r;
+#pragma unroll
+      for (int i = j + 1; i < m; ++i) {
+        float t = (float)Q[i * m + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
+        L[i * m + j] = t * r;
+      }
+    }
+    return ok;
+  }
+
   // ------------------------------------------------------------------------
   // One backward knot for sub-warp groups (2 <= G < 32), split by columns.
   //   1. Q_uu and Q_u: lane c forms column c of V B in registers, then
   //      column c of Q_uu = l_uu + B^T (V B).
-  //   2. Every lane factors the group's Q_uu in float64 (chol_nb) while lane
+  //   2. Every lane factors the group's Q_uu (in float32 when its pivots
+  //      clear chol_f32's test, else in float64: chol_nb) while lane
   //      j forms column j of V A in registers and from it column j of Q_xx,
   //      of Q_ux and Q_x[j]: no barrier between the products, no branch, and
   //      no lane waits for a leader's float64 chain.  Q_xx goes to the V A
@@ -474,7 +534,12 @@ struct Solver {
     static_assert(G >= 2 && G < 32, "sub-warp groups");
     constexpr int NT = n * (n + 1) / 2;
     R* QX = w.VA;                                         // Q_xx, full (mirrored)
-    // 1. Q_uu (float64 and R copies) and Q_u
+    // the float64 copy of Q_uu is read only by the float64 factors (FP64
+    // mode, the Levenberg-Marquardt variant) and by the native float64
+    // refinement residual; the fallback of the float32 factor converts Q_uu
+    // itself
+    const bool q64 = sizeof(R) == 8 || a.lm || a.refine == 2;
+    // 1. Q_uu (R copy, and the float64 copy when q64) and Q_u
 #pragma unroll
     for (int s = 0; s < (m + G - 1) / G; ++s) {
       const int c0 = g.lane + s * G;
@@ -494,7 +559,7 @@ struct Solver {
 #pragma unroll
         for (int r = 0; r < n; ++r) t += w.Bm[r * m + i] * vb[r];
         if (st) {
-          w.Quu[i * m + c] = (double)t;
+          if (q64) w.Quu[i * m + c] = (double)t;
           w.Quf[i * m + c] = t;
         }
       }
@@ -505,21 +570,24 @@ struct Solver {
     }
     g.sync();
     TO_TICK(2);
-    // 2. the float64 factor on every lane, interleaved with the column products
+    // 2. the factor on every lane, interleaved with the column products
     double Lr[m * m];
+    float L32[m * m];
     double mu = 0;
     bool ok;
+    bool f32 = false;            // the float32 factor L32 was accepted
     constexpr bool kSeed = sizeof(R) == 4;
     {
       double Q[m * m];
       R mxr = R(0);
 #pragma unroll
       for (int i = 0; i < m; ++i) mxr = max_abs(mxr, w.Quf[i * m + i]);
+      auto load_q64 = [&]() {
 #pragma unroll
-      for (int i = 0; i < m; ++i)
+        for (int i = 0; i < m; ++i)
 #pragma unroll
-        for (int j = 0; j <= i; ++j) Q[i * m + j] = w.Quu[i * m + j];
-      const double mx = (double)mxr;
+          for (int j = 0; j <= i; ++j) Q[i * m + j] = w.Quu[i * m + j];
+      };
       auto cols = [&]() {
 #pragma unroll
         for (int s = 0; s < (n + G - 1) / G; ++s) {
@@ -555,22 +623,42 @@ struct Solver {
         }
       };
       if (a.lm) {
+        load_q64();
+        const double mx = (double)mxr;
         mu = mu_lm;
         ok = chol_nb<kSeed, true>(Q, mu, 1e-12 * (mx + mu), Lr);
         cols();
         ok = ok & (mxr == mxr) & (mxr <= R(3.0e38));
+      } else if constexpr (sizeof(R) == 4) {
+        // mixed, clipped Hessians: float32 when every pivot is well clear of
+        // zero; any other Q_uu goes to the float64 factor and its guard below
+        ok = chol_f32(w.Quf, mxr, L32);
+        cols();
+        ok = ok & (mxr > R(0)) & (mxr <= R(3.0e38));
+        f32 = true;
       } else {
+        load_q64();
+        const double mx = (double)mxr;
         ok = chol_nb<kSeed, false>(Q, 0.0, 1e-12 * mx, Lr);
         cols();
         ok = ok & (mxr > R(0)) & (mxr <= R(3.0e38));
       }
     }
-    // the guarded path (a failed pivot test, or a pivot outside the seed's
-    // range): the float64 factor with the shift schedule, as in factor()
+    // the guarded path (a failed pivot test, a pivot outside the seed's
+    // range, or a float32 factor not accepted): the float64 factor with the
+    // shift schedule, as in factor()
     R Lf[m * m];
     int flag = 0;
     if (!ok && act) {          // (an idle group's stale Q_uu takes no guarded retries)
-      flag = factor(w.Quu, w.Quf, a.lm, mu_lm, Lr, Lf, mu);
+      double Qd[m * m];
+#pragma unroll
+      for (int i = 0; i < m * m; ++i) Qd[i] = q64 ? w.Quu[i] : (double)w.Quf[i];
+      flag = factor(Qd, w.Quf, a.lm, mu_lm, Lr, Lf, mu);
+    } else if (f32) {
+#pragma unroll
+      for (int i = 0; i < m; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) Lf[i * m + j] = (R)L32[i * m + j];
     } else {
 #pragma unroll
       for (int i = 0; i < m; ++i)
@@ -818,19 +906,19 @@ struct Solver {
     const R eps = (R)a.eps;
     double* vx = (a.vx && a.want_vx) ? a.vx : nullptr;
     R V[n * n], v[n], nx[RS];
-    ld_vec<RS>(rec(traj, base, T, cur), nx);
+    ld_vec<RS>(rec(a, traj, base, T, cur), nx);
     Sys::terminal_derivs(P, nx, eps, V, v);
     if (vx)
 #pragma unroll
-      for (int i = 0; i < n; ++i) vx[(base + T) * n + i] = (double)v[i];
-    ld_vec<RS>(rec(traj, base, T - 1, cur), nx);
+      for (int i = 0; i < n; ++i) vx_at(a, vx, base + T)[i] = (double)v[i];
+    ld_vec<RS>(rec(a, traj, base, T - 1, cur), nx);
     for (int k = T - 1; k >= 0; --k) {
       R x[n], u[m];
 #pragma unroll
       for (int i = 0; i < n; ++i) x[i] = nx[i];
 #pragma unroll
       for (int i = 0; i < m; ++i) u[i] = nx[n + i];
-      if (k >= 1) ld_vec<RS>(rec(traj, base, k - 1, cur), nx);
+      if (k >= 1) ld_vec<RS>(rec(a, traj, base, k - 1, cur), nx);
       R A[n * n], Bm[n * m], lxx[n * n], lx[n], luu[m * m], lu[m];
       Sys::derivs_lane(P, x, u, eps, A, Bm, lxx, lx, luu, lu);
       TO_TICK(1);
@@ -935,9 +1023,9 @@ struct Solver {
 #pragma unroll
         for (int r = 0; r < m; ++r) t += Qux[r * n + i] * g[m * n + r];
         v[i] = t;
-        if (vx) vx[(base + k) * n + i] = (double)t;
+        if (vx) vx_at(a, vx, base + k)[i] = (double)t;
       }
-      st_vec<GS>(gains + (base + k) * GS, g);
+      st_vec<GS>(grec_at(a, gains, base + k), g);
       TO_TICK(4);
     }
   }
@@ -1052,7 +1140,20 @@ struct Solver {
   }
 
   // knot record k of trajectory slot s of the instance whose first record is base
-  TO_DEV static R* rec(R* traj, long long base, int k, int s) { return traj + ((base + k) * NS + s) * RS; }
+  TO_DEV static R* rec(const SolveArgs& a, R* traj, long long base, int k, int s) {
+    const long long kn = ck(a, base + k, a.knots_cap, CK_RECORD);
+    return traj + (kn * NS + ck(a, s, NS, CK_SLOT)) * RS;
+  }
+  // the gain record of knot kn, the V_x row of knot kn, the derivative scratch of knot kn
+  TO_DEV static R* grec_at(const SolveArgs& a, R* gains, long long kn) {
+    return gains + ck(a, kn, a.knots_cap, CK_GAINS) * GS;
+  }
+  TO_DEV static double* vx_at(const SolveArgs& a, double* vx, long long kn) {
+    return vx + ck(a, kn, a.knots_cap, CK_VX) * n;
+  }
+  TO_DEV static R* dscr_at(const SolveArgs& a, long long kn) {
+    return reinterpret_cast<R*>(a.dscr) + ck(a, kn, a.knots_cap, CK_DSCR) * a.kscr;
+  }
 
   // ------------------------------------------------------------------------
   // the kernel body
@@ -1111,15 +1212,17 @@ struct Solver {
           if (q >= 0 && a.serve.ring) {
             __threadfence_system();
             const volatile ServeDesc& d = a.serve.ring[q % a.serve.ring_size];
-            inst = d.seat;
+            inst = (int)ck(a, d.seat, a.B, CK_SEAT);
             T = d.T;
+            if (!ck_ok(a, T - 1, a.T_max, CK_HORIZON)) T = 1;
             base = (long long)inst * (a.T_max + 1);
             sq = q;
             if (g.lane == 0) a.serve.seat_T[inst] = T;
             mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0; mu_lm = kMu0;
           } else if (q >= 0) {
-            inst = a.order[q];
+            inst = (int)ck(a, a.order[q], a.B, CK_ORDER);
             T = a.T[inst];
+            if (!ck_ok(a, T - 1, a.T_max, CK_HORIZON)) T = 1;
             base = a.toff[inst];
             mode = M_NEW; iter = 0; status = 0; flags = 0; J = 0; cur = 0; mu_lm = kMu0;
           } else if (q == -2) {
@@ -1156,7 +1259,7 @@ struct Solver {
       bool release = false;
       bool retry = false;   // Levenberg-Marquardt: redo the backward pass with a larger mu
       // ---- a forced sequence ends with -1
-      if (mode == M_RUN && forced_mode && a.forced[(size_t)inst * a.max_iter + iter] < 0) {
+      if (mode == M_RUN && forced_mode && a.forced[(size_t)inst * a.max_iter + ck(a, iter, a.max_iter, CK_FORCED)] < 0) {
         status = ST_MAX_ITER;
         if (a.want_vx) mode = M_FINAL; else release = true;
       }
@@ -1173,16 +1276,16 @@ struct Solver {
           R pb[PB];
           if (bw) {
             if (g.lane == 0) {
-              const R* r = rec(traj, base, T, cur);
+              const R* r = rec(a, traj, base, T, cur);
               R xT[n];
 #pragma unroll
               for (int i = 0; i < n; ++i) xT[i] = r[i];
               Sys::terminal_derivs(P, xT, (R)a.eps, w.V, w.v);
               if (a.vx && a.want_vx)
-                for (int i = 0; i < n; ++i) a.vx[(base + T) * n + i] = (double)w.v[i];
+                for (int i = 0; i < n; ++i) vx_at(a, a.vx, base + T)[i] = (double)w.v[i];
             }
             if constexpr (!Sys::kStoredDerivs) {
-              const R* r = rec(traj, base, T - 1, cur);
+              const R* r = rec(a, traj, base, T - 1, cur);
 #pragma unroll
               for (int s = 0; s < PB; ++s) {
                 const int e = g.lane + s * G;
@@ -1197,18 +1300,18 @@ struct Solver {
               const R eps = (R)a.eps;
               // the next knot's record is loaded (16-byte vectors) while this one computes
               R nr[RS];
-              if (g.lane < T) ld_vec<RS>(rec(traj, base, g.lane, cur), nr);
+              if (g.lane < T) ld_vec<RS>(rec(a, traj, base, g.lane, cur), nr);
               for (int k = g.lane; k < T; k += G) {
                 R x[n], u[m];
 #pragma unroll
                 for (int i = 0; i < n; ++i) x[i] = nr[i];
 #pragma unroll
                 for (int i = 0; i < m; ++i) u[i] = nr[n + i];
-                if (k + G < T) ld_vec<RS>(rec(traj, base, k + G, cur), nr);
+                if (k + G < T) ld_vec<RS>(rec(a, traj, base, k + G, cur), nr);
                 R d[Sys::kDerivStride];
                 Sys::derivs_lane(P, x, u, eps, d, d + n * n, d + n * n + n * m, d + 2 * n * n + n * m,
                                  d + 2 * n * n + n * m + n, d + 2 * n * n + n * m + n + m * m);
-                st_vec<Sys::kDerivStride>(reinterpret_cast<R*>(a.dscr) + (base + k) * a.kscr, d);
+                st_vec<Sys::kDerivStride>(dscr_at(a, base + k), d);
               }
             }
           }
@@ -1216,20 +1319,20 @@ struct Solver {
             // every lane: the substep primal chains of its knots (bw is uniform over a group of whole warps)
             if (bw)
               for (int k = g.lane; k < T; k += G) {
-                const R* r = rec(traj, base, k, cur);
+                const R* r = rec(a, traj, base, k, cur);
                 R x[n], u[m];
 #pragma unroll
                 for (int i = 0; i < n; ++i) x[i] = r[i];
 #pragma unroll
                 for (int i = 0; i < m; ++i) u[i] = r[n + i];
-                Sys::primal_knot(P, x, u, reinterpret_cast<R*>(a.dscr) + (base + k) * a.kscr);
+                Sys::primal_knot(P, x, u, dscr_at(a, base + k));
               }
           }
           g.sync();
           if constexpr (Sys::kStoredDerivs) {
             // the last knot's stored block (written above by the group's lanes)
             if (bw) {
-              const R* d = reinterpret_cast<const R*>(a.dscr) + (base + T - 1) * a.kscr;
+              const R* d = dscr_at(a, base + T - 1);
 #pragma unroll
               for (int s = 0; s < PB; ++s) {
                 const int e = g.lane + s * G;
@@ -1242,14 +1345,13 @@ struct Solver {
             const bool act = bw && k < T;
             const bool act_next = bw && k >= 1 && k - 1 < T;
             const long long kk = base + (act ? k : 0);
-            const R* rn = rec(traj, base, act_next ? k - 1 : 0, cur);
+            const R* rn = rec(a, traj, base, act_next ? k - 1 : 0, cur);
             // rigid trees: the knot's stored substep primals; planar arm: the
             // next knot's stored derivative block (this knot's is in pb)
             const long long kd = Sys::kStoredDerivs ? base + (act_next ? k - 1 : 0) : kk;
-            const R* kprim = (Sys::kKnotParallel || Sys::kStoredDerivs) ? reinterpret_cast<const R*>(a.dscr) + kd * a.kscr
-                                                                          : nullptr;
-            const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, gains + kk * GS,
-                                        (a.vx && a.want_vx && act) ? a.vx + kk * n : nullptr, mu_lm, timer, tlast,
+            const R* kprim = (Sys::kKnotParallel || Sys::kStoredDerivs) ? dscr_at(a, kd) : nullptr;
+            const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, grec_at(a, gains, kk),
+                                        (a.vx && a.want_vx && act) ? vx_at(a, a.vx, kk) : nullptr, mu_lm, timer, tlast,
                                         kprim);
             if (f == 1) flags |= ST_FLAG_REG;
             // Levenberg-Marquardt: any failed factor (pivot test, or a
@@ -1287,7 +1389,7 @@ struct Solver {
         const bool actor_rnd = Sys::kActor && a.actor_w != nullptr && a.U_init == nullptr &&
                                !g.uniform_all(mode != M_NEW);
         const int nr = single ? 1 : (a.n_alpha + LW - 1) / LW;
-        const int jforced = (mode == M_RUN && forced_mode && fwd) ? a.forced[(size_t)inst * a.max_iter + iter] : 0;
+        const int jforced = (mode == M_RUN && forced_mode && fwd) ? a.forced[(size_t)inst * a.max_iter + ck(a, iter, a.max_iter, CK_FORCED)] : 0;
         // the trip count is the same for every group of the warp / CTA (each
         // round holds barriers); groups that need fewer rounds idle through
         for (int round = 0; round < kRounds; ++round) {
@@ -1311,7 +1413,7 @@ struct Solver {
                 xlo[i] = kLo ? (R)(x0 - (double)xh[i]) : R(0);
               }
             } else {
-              const R* r = rec(traj, base, 0, cur);
+              const R* r = rec(a, traj, base, 0, cur);
 #pragma unroll
               for (int i = 0; i < n; ++i) {
                 xh[i] = r[i];
@@ -1321,10 +1423,10 @@ struct Solver {
           }
           if (nominal) {
             if constexpr (kLane) {
-              ld_vec<RS>(rec(traj, base, 0, cur), pr);
-              ld_vec<GS>(gains + base * GS, pg);
+              ld_vec<RS>(rec(a, traj, base, 0, cur), pr);
+              ld_vec<GS>(grec_at(a, gains, base), pg);
             } else {
-              prefetch_fwd(g, pf, rec(traj, base, 0, cur), gains + base * GS);
+              prefetch_fwd(g, pf, rec(a, traj, base, 0, cur), grec_at(a, gains, base));
             }
           }
           const int kr = g.uniform_max(need ? T : 0, &w.sel);
@@ -1338,14 +1440,14 @@ struct Solver {
 #pragma unroll
                 for (int i = 0; i < GS; ++i) cg[i] = pg[i];
                 if (k + 1 < T) {
-                  ld_vec<RS>(rec(traj, base, k + 1, cur), pr);
-                  ld_vec<GS>(gains + (base + k + 1) * GS, pg);
+                  ld_vec<RS>(rec(a, traj, base, k + 1, cur), pr);
+                  ld_vec<GS>(grec_at(a, gains, base + k + 1), pg);
                 }
               }
             } else {
               if (act && nominal) store_fwd(g, w, pf);
               g.sync();
-              if (act && nominal && k + 1 < T) prefetch_fwd(g, pf, rec(traj, base, k + 1, cur), gains + (base + k + 1) * GS);
+              if (act && nominal && k + 1 < T) prefetch_fwd(g, pf, rec(a, traj, base, k + 1, cur), grec_at(a, gains, base + k + 1));
             }
             if constexpr (Sys::kActor) {
               // warm start from the actor policy u_k = pi(x_k): the group
@@ -1372,13 +1474,13 @@ struct Solver {
                 if (!from_actor)
 #pragma unroll
                   for (int i = 0; i < m; ++i)
-                    uh[i] = a.U_init ? (R)a.U_init[((size_t)inst * a.T_max + k) * m + i] : R(0);
+                    uh[i] = a.U_init ? (R)a.U_init[((size_t)inst * a.T_max + ck(a, k, a.T_max, CK_UINIT)) * m + i] : R(0);
               } else {
                 if constexpr (kLane) policy_regs(cr, cg, alpha, xh, xlo, uh);
                 else policy(w, alpha, xh, xlo, uh);
               }
               // the padding too: whole 32-byte sectors reach L2 without a read
-              put_record(rec(traj, base, k, slot), xh, uh, xlo);
+              put_record(rec(a, traj, base, k, slot), xh, uh, xlo);
               if constexpr (!Sys::template kGroupStep<G>) Jc.add(Sys::cost_step2(P, xh, xlo, uh));
             }
             if constexpr (Sys::template kGroupStep<G>) {
@@ -1393,7 +1495,7 @@ struct Solver {
           int best = 0x7fffffff;
           if (mine) {
             const R u0[m] = {};                                 // no control at the terminal knot
-            put_record(rec(traj, base, T, slot), xh, u0, xlo);
+            put_record(rec(a, traj, base, T, slot), xh, u0, xlo);
             Jc.add(Sys::terminal_cost(P, xh));
             Jt = Jc.value();
             if (single || Jt < J) best = single ? 0 : j;   // strict decrease, compared in float64
@@ -1438,8 +1540,8 @@ struct Solver {
         cur = newslot;
         mu_lm = fmax(mu_lm / kMuFactor, kMuMin);
         if (g.lane == 0) {
-          a.ahist[(size_t)inst * a.max_iter + iter - 1] = jstar;
-          a.Jhist[(size_t)inst * (a.max_iter + 1) + iter] = Jnew;
+          a.ahist[(size_t)inst * a.max_iter + ck(a, iter - 1, a.max_iter, CK_HIST)] = jstar;
+          a.Jhist[(size_t)inst * (a.max_iter + 1) + ck(a, iter, a.max_iter + 1, CK_HIST)] = Jnew;
         }
         const double rel = (J - Jnew) / fmax(fabs(J), 1e-300);
         J = Jnew;

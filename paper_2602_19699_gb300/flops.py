@@ -169,8 +169,22 @@ def solve_flops(sys: int, n: int, m: int, T: np.ndarray, iters: np.ndarray, stat
     return total
 
 
-def solve_flops_fp64(m: int, T: np.ndarray, iters: np.ndarray, status: np.ndarray) -> float:
-    """The float64 FLOPs of a mixed solve (one Cholesky of Q_uu per backward knot)."""
+def fp64_factor_in_mixed(group_lanes: int, lm: bool = False) -> bool:
+    """Whether a mixed solve factors every Q_uu in float64.  Groups of 2 to 31
+    lanes with clipped Hessians factor in float32 and fall back to the float64
+    factor only for a Q_uu with a pivot below 2^-10 of its largest diagonal
+    entry (7e-6 of the backward knots on the planar-arm bench workload; not
+    counted here); single-lane groups, whole-warp groups and the
+    Levenberg-Marquardt variant factor in float64."""
+    return lm or not (2 <= group_lanes < 32)
+
+
+def solve_flops_fp64(m: int, T: np.ndarray, iters: np.ndarray, status: np.ndarray, group_lanes: int = 1,
+                     lm: bool = False) -> float:
+    """The float64 FLOPs of a mixed solve (one Cholesky of Q_uu per backward
+    knot where the factor runs in float64, see fp64_factor_in_mixed)."""
+    if not fp64_factor_in_mixed(group_lanes, lm):
+        return 0.0
     T = np.asarray(T, dtype=np.float64)
     failed = (np.asarray(status) & 15) == 3
     return float(np.sum(T * (np.asarray(iters) + failed)) * cholesky_fp64_flops(m))
