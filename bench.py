@@ -276,7 +276,8 @@ def run_gb300(args):
     tune_opts = P.to_default_opts(prec=P.TO_MIXED, max_iter=3, tol_rel=TOL, n_alpha=N_ALPHA)
     tune_rows = P.totune(problem, b.x0, b.T, tune_opts)
     opts.group_lanes, opts.groups_per_block = tune_opts.group_lanes, tune_opts.groups_per_block
-    _log(f"autotune: G={opts.group_lanes} x {opts.groups_per_block} per CTA "
+    opts.stage_depth = tune_opts.stage_depth
+    _log(f"autotune: G={opts.group_lanes} x {opts.groups_per_block} per CTA, staging depth {opts.stage_depth} "
          f"({len(tune_rows)} shapes, {min(r['ms'] for r in tune_rows):.1f} .. {max(r['ms'] for r in tune_rows):.1f} ms)")
     batch = P.tocreate_batch(problem, B, B * (T_MAX + 1), opts)
     dev = torch.device("cuda", local)
@@ -519,7 +520,7 @@ def run_gb300(args):
             "batch_per_gpu": B, "knots_per_gpu": knots, "parallelism": f"independent instances x{n}",
             "l2": "flushed between steps (512 MB write); working set ~1.7 GB > L2",
             "launch": f"persistent kernel, {opts.group_lanes} lanes per instance, {opts.groups_per_block} "
-                      f"instances per CTA (autotuned)",
+                      f"instances per CTA, staging depth {opts.stage_depth} (autotuned)",
         },
         "raw_solves_per_s": job_throughput(B, t_step, n),
         "within_tol": {"cost_tol": COST_TOL, "sample": int(len(idx)), "fraction": frac_mixed,
@@ -532,9 +533,11 @@ def run_gb300(args):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_max / args.steps * 1e3,
                 "api": "tograph_launch of a captured solve (H2D from pinned staging, sort, solver, gather, D2H)",
                 "kernels_per_step": int(e2e_launches), "results_equal_device_solve": e2e_same},
-        "autotune": {"chosen": [int(opts.group_lanes), int(opts.groups_per_block)],
+        "autotune": {"chosen": [int(opts.group_lanes), int(opts.groups_per_block), int(opts.stage_depth)],
                      "calibration": "the workload itself, max_iter=3",
-                     "rows": [[r["group_lanes"], r["groups_per_block"], round(r["ms"], 2)] for r in tune_rows]},
+                     "columns": ["group_lanes", "groups_per_block", "stage_depth", "ms"],
+                     "rows": [[r["group_lanes"], r["groups_per_block"], r["stage_depth"], round(r["ms"], 2)]
+                              for r in tune_rows]},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_mix, "unit": "TFLOP/s",
                      "frac": achieved / peak_mix, "traffic": traffic,

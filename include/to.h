@@ -197,6 +197,17 @@ typedef struct {
                              (not below 1e-8) after an accepted step;
                              mu > 1e10 stops the instance with LS_FAIL.
                              eps_clip is ignored                              */
+  int stage_depth;        /* knots of look-ahead with which a group fetches
+                             what it reads next (the backward pass's knot
+                             record or stored derivative block, the forward
+                             pass's record and gains) into registers: 1 or 2
+                             (2 only where the system offers it: the planar
+                             arm's groups of 4 or more lanes; else
+                             TO_ERR_ARG); 0 = the totune choice, else 1.
+                             The arithmetic is the same at every depth:
+                             results agree to the rounding of the compiler's
+                             multiply-add fusion, which may differ between
+                             kernel instantiations                            */
 } to_solver_opts;
 
 /* to_solver_opts.reg */
@@ -204,7 +215,7 @@ enum { TO_REG_CLIP = 0, TO_REG_LM = 1 };
 
 /* Defaults: max_iter 100, tol_rel 1e-8, eps_clip 1e-8, n_alpha 16,
  * alpha_decay 0.5, TO_MIXED, refine 1, no forcing, want_vx 0, no budget,
- * autotuned launch shape. */
+ * autotuned launch shape and staging depth. */
 void to_default_opts(to_solver_opts* opts);
 
 /* One instance family of the OCP of Sec. II, Eq. 1: the system's dynamics
@@ -411,15 +422,16 @@ int tosolve_batch_noalloc(to_problem p, int B, const double* d_x0, const int* d_
 
 /*
  * Launch-shape autotuner.  The solver kernel's shape -- threads per instance
- * (group_lanes, from the system's supported set) and instances per CTA
- * (groups_per_block) -- trades per-instance parallelism against occupancy
- * and register pressure, and the best point differs per system and
- * precision.  totune times every valid shape on a calibration batch (host
+ * (group_lanes, from the system's supported set), instances per CTA
+ * (groups_per_block) and the staging depth (stage_depth, where the system
+ * offers more than one) -- trades per-instance parallelism against
+ * occupancy, register pressure and load latency, and the best point differs
+ * per system and precision.  totune times every valid shape on a calibration batch (host
  * x0: B x n, T: B; solved with *opts, whose max_iter may be smaller than the
  * production one) with CUDA events on a stream of its own, after one untimed
  * warm-up solve per shape.  The fastest shape is written into
- * opts->group_lanes / groups_per_block and cached in the problem for
- * opts->prec: later solves that leave both at 0 use it.  rows (may be NULL)
+ * opts->group_lanes / groups_per_block / stage_depth and cached in the
+ * problem for opts->prec: later solves that leave all three at 0 use it.  rows (may be NULL)
  * receives up to max_rows measured shapes; *n_rows how many were measured.
  * The calibration batch should fill the GPU (several instances per SM) so
  * the choice holds for large batches.  With the environment variable
@@ -434,6 +446,7 @@ typedef struct {
   int grid;               /* CTAs launched                                     */
   int ctas_per_sm;        /* resident CTAs per SM at this shape                */
   double ms;              /* device time of one solve of the calibration batch */
+  int stage_depth;        /* staging depth of this shape                       */
 } to_tune_row;
 int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* opts, to_tune_row* rows,
            int max_rows, int* n_rows);

@@ -48,7 +48,7 @@ class to_solver_opts(C.Structure):
                 ("alpha_decay", C.c_double), ("prec", C.c_int), ("refine", C.c_int),
                 ("forced_alpha", C.POINTER(C.c_int)), ("want_vx", C.c_int), ("hbm_budget_bytes", C.c_size_t),
                 ("group_lanes", C.c_int), ("groups_per_block", C.c_int), ("profile_phases", C.c_int),
-                ("reg", C.c_int)]
+                ("reg", C.c_int), ("stage_depth", C.c_int)]
 
 
 _lib = None
@@ -154,7 +154,7 @@ class Ranker:
 
 class to_tune_row(C.Structure):
     _fields_ = [("group_lanes", C.c_int), ("groups_per_block", C.c_int), ("grid", C.c_int),
-                ("ctas_per_sm", C.c_int), ("ms", C.c_double)]
+                ("ctas_per_sm", C.c_int), ("ms", C.c_double), ("stage_depth", C.c_int)]
 
 
 def totune(problem: "Problem", x0, T, opts: "to_solver_opts", max_rows: int = 64):
@@ -167,7 +167,7 @@ def totune(problem: "Problem", x0, T, opts: "to_solver_opts", max_rows: int = 64
     n = C.c_int()
     _check(lib().totune(problem.handle, int(T.size), _ptr(x0), _ptr(T), C.byref(opts), rows, max_rows, C.byref(n)))
     return [{"group_lanes": r.group_lanes, "groups_per_block": r.groups_per_block, "grid": r.grid,
-             "ctas_per_sm": r.ctas_per_sm, "ms": r.ms} for r in rows[:n.value]]
+             "ctas_per_sm": r.ctas_per_sm, "ms": r.ms, "stage_depth": r.stage_depth} for r in rows[:n.value]]
 
 
 class Graph:

@@ -429,20 +429,23 @@ static int check_opts(const to_solver_opts* o) {
   if (!(o->eps_clip >= 0)) return fail(TO_ERR_ARG, "opts: eps_clip must be >= 0");
   if (o->prec != TO_FP64 && o->prec != TO_MIXED) return fail(TO_ERR_ARG, "opts: prec must be TO_FP64 or TO_MIXED");
   if (o->reg != TO_REG_CLIP && o->reg != TO_REG_LM) return fail(TO_ERR_ARG, "opts: reg must be TO_REG_CLIP or TO_REG_LM");
+  if (o->stage_depth < 0 || o->stage_depth > 2) return fail(TO_ERR_ARG, "opts: stage_depth must be 0, 1 or 2");
   return TO_OK;
 }
 
-// launch shape of a solve: group size, groups per CTA, CTAs (persistent:
-// at most frac of the CTAs the GPU holds resident at once)
+// launch shape of a solve: group size, groups per CTA, staging depth, CTAs
+// (persistent: at most frac of the CTAs the GPU holds resident at once)
 static int resolve_shape(to_problem p, const to_solver_opts* o, int B, double frac, int* G_out, int* gpb_out,
-                         int* grid_out, int* bps_out) {
+                         int* grid_out, int* bps_out, int* depth_out) {
   const SysOps* ops = p->ops;
   const int prec = o->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
-  int G = o->group_lanes, gpb = o->groups_per_block;
-  if (!G && !gpb && p->tuned_G[prec]) {
+  int G = o->group_lanes, gpb = o->groups_per_block, depth = o->stage_depth;
+  if (!G && !gpb && !depth && p->tuned_G[prec]) {
     G = p->tuned_G[prec];
     gpb = p->tuned_gpb[prec];
+    depth = p->tuned_depth[prec];
   }
+  if (!depth) depth = 1;
   if (!G) G = ops->default_G;
   if (!gpb) {
     gpb = ops->default_gpb[prec];
@@ -454,9 +457,11 @@ static int resolve_shape(to_problem p, const to_solver_opts* o, int B, double fr
   if (G <= 32 && (G * gpb) % 32 != 0) return fail(TO_ERR_ARG, "opts: groups_per_block * group_lanes must be a multiple of 32");
   if (G > 32 && gpb != 1) return fail(TO_ERR_ARG, "opts: groups_per_block must be 1 when group_lanes > 32");
   if (G * gpb > kMaxCtaThreads) return fail(TO_ERR_ARG, "opts: CTA larger than 256 threads");
+  if (depth > ops->max_depth || (depth > 1 && G == 1))
+    return fail(TO_ERR_ARG, "opts: stage_depth not offered by this system at this group size");
   size_t smem = 0;
   int bps = 0;
-  TO_CK(ops->occupancy(prec, G, gpb, &smem, &bps));
+  TO_CK(ops->occupancy(prec, G, depth, gpb, &smem, &bps));
   if (bps < 1) return fail(TO_ERR_ARG, "opts: launch shape does not fit on an SM");
   int dev = 0, sms = 0;
   TO_CK(cudaGetDevice(&dev));
@@ -466,6 +471,7 @@ static int resolve_shape(to_problem p, const to_solver_opts* o, int B, double fr
   *gpb_out = gpb;
   *grid_out = std::max(1, std::min((B + gpb - 1) / gpb, cap));
   if (bps_out) *bps_out = bps;
+  if (depth_out) *depth_out = depth;
   return TO_OK;
 }
 
@@ -517,8 +523,8 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
   // a serving kernel, or a member of a multi-system graph, takes its share of
   // the resident CTAs, so the kernels of the other problems run beside it
   const double frac = serve ? serve->grid_frac : b->grid_frac;
-  int G = 0, gpb = 0, grid = 0;
-  int rc = resolve_shape(p, o, B, frac, &G, &gpb, &grid, nullptr);
+  int G = 0, gpb = 0, grid = 0, depth = 1;
+  int rc = resolve_shape(p, o, B, frac, &G, &gpb, &grid, nullptr, &depth);
   if (rc) return rc;
 
   SolveArgs a{};
@@ -537,7 +543,7 @@ static int launch_solve(to_batch b, int B, const double* d_x0, const int* d_T, c
                                       b->queue, b->J, b->iters);
     TO_CK(cudaGetLastError());
   }
-  TO_CK(ops->launch(prec, G, gpb, grid, s, a));
+  TO_CK(ops->launch(prec, G, depth, gpb, grid, s, a));
   b->B = B;
   b->max_iter = o->max_iter;
   b->prec = o->prec;
@@ -553,8 +559,9 @@ int to_fail(int code, const std::string& msg) { return fail(code, msg); }
 
 int to_check_opts(const to_solver_opts* o) { return check_opts(o); }
 
-int to_resolve_shape(to_problem p, const to_solver_opts* o, int B, double frac, int* G, int* gpb, int* grid, int* bps) {
-  return resolve_shape(p, o, B, frac, G, gpb, grid, bps);
+int to_resolve_shape(to_problem p, const to_solver_opts* o, int B, double frac, int* G, int* gpb, int* grid, int* bps,
+                     int* depth) {
+  return resolve_shape(p, o, B, frac, G, gpb, grid, bps, depth);
 }
 
 int to_ensure_workspace(to_batch b, const to_solver_opts* o, bool want_traj) {

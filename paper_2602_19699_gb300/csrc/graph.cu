@@ -38,7 +38,7 @@ struct TuneScratch {
 
 // The persisted choice of the autotuner: when the environment variable
 // TO_TUNE_CACHE names a file, each tuned shape is appended to it as one line
-//   <key> <group_lanes> <groups_per_block> <ms>
+//   <key> <group_lanes> <groups_per_block> <ms> <stage_depth>
 // and a later totune with the same key (in any process) takes the shape from
 // the file instead of timing again.  The key holds what the best shape
 // depends on: the system and its sizes, T_max, the batch size and the mean
@@ -62,7 +62,7 @@ std::string tune_key(to_problem p, int B, const int* T, const to_solver_opts* o)
   return key;
 }
 
-bool tune_cache_lookup(const std::string& key, int* G, int* gpb, double* ms) {
+bool tune_cache_lookup(const std::string& key, int* G, int* gpb, double* ms, int* depth) {
   const char* path = std::getenv("TO_TUNE_CACHE");
   if (!path || !*path || key.empty()) return false;
   FILE* f = std::fopen(path, "r");
@@ -71,10 +71,12 @@ bool tune_cache_lookup(const std::string& key, int* G, int* gpb, double* ms) {
   bool found = false;
   while (std::fgets(line, sizeof line, f)) {
     char k[600];
-    int g = 0, b = 0;
+    int g = 0, b = 0, d = 1;
     double t = 0;
-    if (std::sscanf(line, "%599s %d %d %lf", k, &g, &b, &t) == 4 && key == k) {
+    const int got = std::sscanf(line, "%599s %d %d %lf %d", k, &g, &b, &t, &d);
+    if (got >= 4 && key == k) {
       *G = g; *gpb = b; *ms = t;          // the last entry for a key wins
+      *depth = got == 5 ? d : 1;
       found = true;
     }
   }
@@ -82,12 +84,12 @@ bool tune_cache_lookup(const std::string& key, int* G, int* gpb, double* ms) {
   return found;
 }
 
-void tune_cache_store(const std::string& key, int G, int gpb, double ms) {
+void tune_cache_store(const std::string& key, int G, int gpb, double ms, int depth) {
   const char* path = std::getenv("TO_TUNE_CACHE");
   if (!path || !*path || key.empty()) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %.6f\n", key.c_str(), G, gpb, ms);
+  std::fprintf(f, "%s %d %d %.6f %d\n", key.c_str(), G, gpb, ms, depth);
   std::fclose(f);
 }
 
@@ -109,19 +111,22 @@ int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* 
   const int prec0 = opts->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
   const std::string key = tune_key(p, B, T, opts);
   {
-    int G = 0, gpb = 0;
+    int G = 0, gpb = 0, depth = 1;
     double ms = 0;
-    if (tune_cache_lookup(key, &G, &gpb, &ms)) {
+    if (tune_cache_lookup(key, &G, &gpb, &ms, &depth)) {
       to_solver_opts o = *opts;
       o.group_lanes = G;
       o.groups_per_block = gpb;
+      o.stage_depth = depth;
       int g2 = 0, b2 = 0, grid = 0, bps = 0;
       if (to_resolve_shape(p, &o, B, 1.0, &g2, &b2, &grid, &bps) == TO_OK) {
         opts->group_lanes = G;
         opts->groups_per_block = gpb;
+        opts->stage_depth = depth;
         p->tuned_G[prec0] = G;
         p->tuned_gpb[prec0] = gpb;
-        if (rows && max_rows > 0) rows[0] = to_tune_row{G, gpb, grid, bps, ms};
+        p->tuned_depth[prec0] = depth;
+        if (rows && max_rows > 0) rows[0] = to_tune_row{G, gpb, grid, bps, ms, depth};
         if (n_rows) *n_rows = max_rows > 0 ? 1 : 0;
         return TO_OK;
       }
@@ -131,6 +136,7 @@ int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* 
   to_solver_opts base = *opts;
   base.group_lanes = 0;
   base.groups_per_block = 0;
+  base.stage_depth = 0;
   rc = tocreate_batch(p, B, knots, &base, &w.b);
   if (rc) return rc;
   rc = to_ensure_workspace(w.b, &base, false);
@@ -143,11 +149,12 @@ int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* 
 
   const SysOps* ops = p->ops;
   const int prec = opts->prec == TO_FP64 ? PREC_FP64 : PREC_MIXED;
-  int best_G = 0, best_gpb = 0, n = 0;
+  int best_G = 0, best_gpb = 0, best_depth = 1, n = 0;
   double best_ms = INFINITY;
   const int cta_threads[] = {32, 64, 128, 256};
   for (int gi = 0; gi < ops->n_groups; ++gi) {
     const int G = ops->groups[gi];
+    for (int depth = 1; depth <= (G > 1 ? ops->max_depth : 1); ++depth)
     for (int threads : cta_threads) {
       if (G > 32 && threads != 32) continue;            // one group per CTA: a single shape
       const int gpb = G > 32 ? 1 : threads / G;
@@ -155,6 +162,7 @@ int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* 
       to_solver_opts o = base;
       o.group_lanes = G;
       o.groups_per_block = gpb;
+      o.stage_depth = depth;
       int g2 = 0, b2 = 0, grid = 0, bps = 0;
       if (to_resolve_shape(p, &o, B, 1.0, &g2, &b2, &grid, &bps) != TO_OK) continue;   // does not fit an SM
       // one untimed solve (first launch of this instantiation), then the timed one
@@ -167,21 +175,24 @@ int totune(to_problem p, int B, const double* x0, const int* T, to_solver_opts* 
       GR_CK(cudaEventSynchronize(w.e1));
       float ms = 0;
       GR_CK(cudaEventElapsedTime(&ms, w.e0, w.e1));
-      if (rows && n < max_rows) rows[n] = to_tune_row{G, gpb, grid, bps, (double)ms};
+      if (rows && n < max_rows) rows[n] = to_tune_row{G, gpb, grid, bps, (double)ms, depth};
       ++n;
       if (ms < best_ms) {
         best_ms = ms;
         best_G = G;
         best_gpb = gpb;
+        best_depth = depth;
       }
     }
   }
   if (!best_G) return to_fail(TO_ERR_ARG, "totune: no launch shape fits an SM");
-  tune_cache_store(key, best_G, best_gpb, best_ms);
+  tune_cache_store(key, best_G, best_gpb, best_ms, best_depth);
   opts->group_lanes = best_G;
   opts->groups_per_block = best_gpb;
+  opts->stage_depth = best_depth;
   p->tuned_G[prec] = best_G;
   p->tuned_gpb[prec] = best_gpb;
+  p->tuned_depth[prec] = best_depth;
   if (n_rows) *n_rows = std::min(n, max_rows);
   return TO_OK;
 }

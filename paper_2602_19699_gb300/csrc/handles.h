@@ -19,6 +19,7 @@ struct to_problem_s {
   size_t knot_scratch[2] = {0, 0};   // per-knot derivative scratch elements (FP64, mixed); 0 = none
   int tuned_G[2] = {0, 0};     // autotuned launch shape per precision (FP64, mixed); 0 = none
   int tuned_gpb[2] = {0, 0};
+  int tuned_depth[2] = {0, 0};
   unsigned long long* chk = nullptr;   // bounds-check report of the checked build (4 words), else null
 };
 
@@ -80,8 +81,9 @@ int to_launch_core(to_batch b, int B, const double* d_x0, const int* d_T, const 
 int to_check_opts(const to_solver_opts* o);
 
 // launch shape of a solve of B instances allowed frac of the resident CTAs
+// (depth may be null: the shape's staging depth)
 int to_resolve_shape(to_problem p, const to_solver_opts* o, int B, double frac, int* G, int* gpb, int* grid,
-                     int* ctas_per_sm);
+                     int* ctas_per_sm, int* depth = nullptr);
 
 // grow the option-dependent workspace (per-iteration history; with
 // want_traj, the X / U gather staging) so that a solve allocates nothing

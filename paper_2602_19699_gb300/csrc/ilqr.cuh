@@ -227,8 +227,14 @@ enum { M_IDLE = 0, M_NEW, M_RUN, M_FINAL, M_DRAINED };
 // (not below kMuMin); beyond kMuMax the instance stops with LS_FAIL
 constexpr double kMu0 = 1e-6, kMuMin = 1e-8, kMuMax = 1e10, kMuFactor = 10.0;
 
-template <class Sys, class R, int G>
+// D is the staging depth: a group fetches the records it will read D knots
+// ahead of the knot that reads them (the backward pass's knot record or
+// stored derivative block, the forward pass's knot record and gains), into a
+// ring of D register sets per lane.  1 or 2; the autotuner picks it.
+template <class Sys, class R, int G, int D = 1>
 struct Solver {
+  static_assert(D == 1 || D == 2, "staging depth 1 or 2");
+  static_assert(G > 1 || D == 1, "a single-lane group stages one knot ahead");
   static constexpr int n = Sys::n, m = Sys::m;
   static constexpr int RS = Layout<Sys, R>::RS, GS = Layout<Sys, R>::GS;
   static constexpr int kLo = Layout<Sys, R>::kLo;
@@ -724,8 +730,9 @@ struct Solver {
 
   // ------------------------------------------------------------------------
   // one knot of the backward pass (all syncs unconditional, work predicated).
-  // The knot's record is in pb (prefetched); the previous knot's record is
-  // fetched into pb while this one computes.  Returns the Cholesky flag.
+  // The knot's record is in pb (prefetched); the record of the knot D
+  // earlier (trec_next; stored blocks: kprim) is fetched into pb while this
+  // one computes (act_next: that knot exists).  Returns the Cholesky flag.
   // ------------------------------------------------------------------------
   TO_DEV static int backward_knot(const Params& P, const Group<G>& g, W& w, bool act, bool act_next,
                                   const SolveArgs& a, R (&pb)[PB], const R* trec_next, R* grec, double* vxrec,
@@ -753,8 +760,8 @@ struct Solver {
     // whole warp or CTA, so act is uniform over every barrier's scope)
     if constexpr (Sys::kStoredDerivs) {
       // the knot's stored block (A, B, l_xx, l_x, l_uu, l_u), prefetched into
-      // pb while the previous knot computed; then the next knot's block is
-      // fetched into pb (kprim: the next knot's block)
+      // pb D knots earlier; then the block of the knot D further on is
+      // fetched into pb (kprim: that block)
       constexpr int DS = Sys::kDerivStride;
       if (act) {
 #pragma unroll
@@ -1273,7 +1280,15 @@ struct Solver {
         } else {
         const int kmax = g.uniform_max(bw ? T : 0, &w.sel);
         if (kmax > 0) {
-          R pb[PB];
+          // the staging ring: knot k's record (or block) sits in slot
+          // (kmax - 1 - k) % D, so the knot loop below indexes it statically
+          R pb[D][PB];
+          auto ring = [&](int k, auto&& f) {
+            const int sl = (kmax - 1 - k) % D;
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+              if (d == sl) f(pb[d]);
+          };
           if (bw) {
             if (g.lane == 0) {
               const R* r = rec(a, traj, base, T, cur);
@@ -1285,11 +1300,17 @@ struct Solver {
                 for (int i = 0; i < n; ++i) vx_at(a, a.vx, base + T)[i] = (double)w.v[i];
             }
             if constexpr (!Sys::kStoredDerivs) {
-              const R* r = rec(a, traj, base, T - 1, cur);
 #pragma unroll
-              for (int s = 0; s < PB; ++s) {
-                const int e = g.lane + s * G;
-                if (e < n + m) pb[s] = r[e];
+              for (int i = 0; i < D; ++i) {
+                if (T - 1 - i < 0) break;
+                const R* r = rec(a, traj, base, T - 1 - i, cur);
+                ring(T - 1 - i, [&](R (&b)[PB]) {
+#pragma unroll
+                  for (int s = 0; s < PB; ++s) {
+                    const int e = g.lane + s * G;
+                    if (e < n + m) b[s] = r[e];
+                  }
+                });
               }
             }
           }
@@ -1330,35 +1351,45 @@ struct Solver {
           }
           g.sync();
           if constexpr (Sys::kStoredDerivs) {
-            // the last knot's stored block (written above by the group's lanes)
-            if (bw) {
-              const R* d = dscr_at(a, base + T - 1);
+            // the last D knots' stored blocks (written above by the group's lanes)
+            if (bw)
 #pragma unroll
-              for (int s = 0; s < PB; ++s) {
-                const int e = g.lane + s * G;
-                if (e < Sys::kDerivStride) pb[s] = d[e];
+              for (int i = 0; i < D; ++i) {
+                if (T - 1 - i < 0) break;
+                const R* d = dscr_at(a, base + T - 1 - i);
+                ring(T - 1 - i, [&](R (&b)[PB]) {
+#pragma unroll
+                  for (int s = 0; s < PB; ++s) {
+                    const int e = g.lane + s * G;
+                    if (e < Sys::kDerivStride) b[s] = d[e];
+                  }
+                });
               }
-            }
           }
           TO_TICK(1);
-          for (int k = kmax - 1; k >= 0; --k) {
-            const bool act = bw && k < T;
-            const bool act_next = bw && k >= 1 && k - 1 < T;
-            const long long kk = base + (act ? k : 0);
-            const R* rn = rec(a, traj, base, act_next ? k - 1 : 0, cur);
-            // rigid trees: the knot's stored substep primals; planar arm: the
-            // next knot's stored derivative block (this knot's is in pb)
-            const long long kd = Sys::kStoredDerivs ? base + (act_next ? k - 1 : 0) : kk;
-            const R* kprim = (Sys::kKnotParallel || Sys::kStoredDerivs) ? dscr_at(a, kd) : nullptr;
-            const int f = backward_knot(P, g, w, act, act_next, a, pb, rn, grec_at(a, gains, kk),
-                                        (a.vx && a.want_vx && act) ? vx_at(a, a.vx, kk) : nullptr, mu_lm, timer, tlast,
-                                        kprim);
-            if (f == 1) flags |= ST_FLAG_REG;
-            // Levenberg-Marquardt: any failed factor (pivot test, or a
-            // non-finite Q_uu once an earlier knot's gains were skipped)
-            // asks for a larger mu; the rest of this pass is discarded
-            if (a.lm) { if (f >= 2) need_mu = true; }
-            else if (f == 2) bad = true;
+          for (int k0 = kmax - 1; k0 >= 0; k0 -= D) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) {      // knot k0 - d reads ring slot d
+              const int k = k0 - d;
+              if (k < 0) break;
+              const bool act = bw && k < T;
+              const bool act_next = bw && k >= D && k - D < T;   // the knot whose record this slot takes next
+              const long long kk = base + (act ? k : 0);
+              const R* rn = rec(a, traj, base, act_next ? k - D : 0, cur);
+              // rigid trees: the knot's stored substep primals; planar arm: the
+              // stored derivative block of the knot D earlier (this knot's is in pb)
+              const long long kd = Sys::kStoredDerivs ? base + (act_next ? k - D : 0) : kk;
+              const R* kprim = (Sys::kKnotParallel || Sys::kStoredDerivs) ? dscr_at(a, kd) : nullptr;
+              const int f = backward_knot(P, g, w, act, act_next, a, pb[d], rn, grec_at(a, gains, kk),
+                                          (a.vx && a.want_vx && act) ? vx_at(a, a.vx, kk) : nullptr, mu_lm, timer,
+                                          tlast, kprim);
+              if (f == 1) flags |= ST_FLAG_REG;
+              // Levenberg-Marquardt: any failed factor (pivot test, or a
+              // non-finite Q_uu once an earlier knot's gains were skipped)
+              // asks for a larger mu; the rest of this pass is discarded
+              if (a.lm) { if (f >= 2) need_mu = true; }
+              else if (f == 2) bad = true;
+            }
           }
         }
         }
@@ -1402,7 +1433,7 @@ struct Solver {
           const bool nominal = need && mode != M_NEW;   // needs the current iterate and gains
           R xh[n], xlo[n];   // the candidate's state as (hi, lo) pairs (lo = 0 in float64)
           Acc<R> Jc;
-          R pf[kLane ? 1 : PF];
+          R pf[D][kLane ? 1 : PF];   // staging ring: knot k's record and gains in slot k % D
           R pr[kLane ? RS : 1], pg[kLane ? GS : 1];   // single lane: next knot's record and gains
           if (mine) {
             if (mode == M_NEW) {
@@ -1426,11 +1457,17 @@ struct Solver {
               ld_vec<RS>(rec(a, traj, base, 0, cur), pr);
               ld_vec<GS>(grec_at(a, gains, base), pg);
             } else {
-              prefetch_fwd(g, pf, rec(a, traj, base, 0, cur), grec_at(a, gains, base));
+#pragma unroll
+              for (int d = 0; d < D; ++d)
+                if (d < T) prefetch_fwd(g, pf[d], rec(a, traj, base, d, cur), grec_at(a, gains, base + d));
             }
           }
           const int kr = g.uniform_max(need ? T : 0, &w.sel);
-          for (int k = 0; k < kr; ++k) {
+          for (int k0 = 0; k0 < kr; k0 += D) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) {        // knot k0 + d reads ring slot d
+            const int k = k0 + d;
+            if (k >= kr) break;
             const bool act = need && k < T;
             R cr[kLane ? RS : 1], cg[kLane ? GS : 1];
             if constexpr (kLane) {
@@ -1445,9 +1482,10 @@ struct Solver {
                 }
               }
             } else {
-              if (act && nominal) store_fwd(g, w, pf);
+              if (act && nominal) store_fwd(g, w, pf[d]);
               g.sync();
-              if (act && nominal && k + 1 < T) prefetch_fwd(g, pf, rec(a, traj, base, k + 1, cur), grec_at(a, gains, base + k + 1));
+              if (act && nominal && k + D < T)
+                prefetch_fwd(g, pf[d], rec(a, traj, base, k + D, cur), grec_at(a, gains, base + k + D));
             }
             if constexpr (Sys::kActor) {
               // warm start from the actor policy u_k = pi(x_k): the group
@@ -1490,6 +1528,7 @@ struct Solver {
               if (act && mine) Jc.add(l);
             }
             if constexpr (!kLane) g.sync();
+          }
           }
           double Jt = 0;
           int best = 0x7fffffff;

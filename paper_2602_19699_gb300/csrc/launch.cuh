@@ -31,8 +31,9 @@ struct SysOps {
   // parse the flat parameter vector into the system's struct in float64 and float32
   int (*parse)(const double* p, size_t np, std::vector<unsigned char>& blob64, std::vector<unsigned char>& blob32,
                std::string& err);
-  cudaError_t (*launch)(int prec, int G, int gpb, int grid, cudaStream_t s, const SolveArgs& a);
-  cudaError_t (*occupancy)(int prec, int G, int gpb, size_t* smem, int* blocks_per_sm);
+  int max_depth;                    // largest staging depth (1 or 2) of its groups of more than one lane
+  cudaError_t (*launch)(int prec, int G, int depth, int gpb, int grid, cudaStream_t s, const SolveArgs& a);
+  cudaError_t (*occupancy)(int prec, int G, int depth, int gpb, size_t* smem, int* blocks_per_sm);
   // per-knot costs of the final trajectories in float64 (critic targets)
   cudaError_t (*knot_costs)(const KnotCostArgs& a, cudaStream_t s);
   // elements of per-knot derivative scratch (stored substep primals) for a
@@ -56,61 +57,75 @@ int multi_group_lanes(int slot);       // lanes per instance of the slot's solve
 
 constexpr int kMaxCtaThreads = 256;
 
-template <class Sys, class R, int G>
+template <class Sys, class R, int G, int D>
 __global__ void __launch_bounds__(kMaxCtaThreads, 1) ilqr_kernel(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Solver<Sys, R, G>::run(a, smem_raw);
+  Solver<Sys, R, G, D>::run(a, smem_raw);
 }
 
-template <class Sys, class R, int G>
+template <class Sys, class R, int G, int D = 1>
 inline size_t solver_smem(int gpb) {
   return ((sizeof(typename Sys::template ParamsT<R>) + 15) / 16) * 16 +
-         (size_t)gpb * sizeof(typename Solver<Sys, R, G>::W);
+         (size_t)gpb * sizeof(typename Solver<Sys, R, G, D>::W);
 }
 
-template <class Sys, class R, int G>
+template <class Sys, class R, int G, int D>
 inline cudaError_t launch_one(int gpb, int grid, cudaStream_t s, const SolveArgs& a) {
   const int threads = G * gpb;
-  const size_t smem = solver_smem<Sys, R, G>(gpb);
-  auto k = ilqr_kernel<Sys, R, G>;
+  const size_t smem = solver_smem<Sys, R, G, D>(gpb);
+  auto k = ilqr_kernel<Sys, R, G, D>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <class Sys, class R, int G>
+template <class Sys, class R, int G, int D>
 inline cudaError_t occupancy_one(int gpb, size_t* smem, int* bps) {
-  *smem = solver_smem<Sys, R, G>(gpb);
-  auto k = ilqr_kernel<Sys, R, G>;
+  *smem = solver_smem<Sys, R, G, D>(gpb);
+  auto k = ilqr_kernel<Sys, R, G, D>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, G * gpb, *smem);
 }
 
-// dispatch on (precision, group size) over a compile-time list of sizes
-template <class Sys, int... Gs>
+// dispatch on (precision, group size) over a compile-time list of sizes, at
+// one staging depth D
+template <class Sys, int D, int... Gs>
 struct Dispatch;
 
-template <class Sys>
-struct Dispatch<Sys> {
+template <class Sys, int D>
+struct Dispatch<Sys, D> {
   static cudaError_t launch(int, int, int, int, cudaStream_t, const SolveArgs&) { return cudaErrorInvalidValue; }
   static cudaError_t occupancy(int, int, int, size_t*, int*) { return cudaErrorInvalidValue; }
 };
 
-template <class Sys, int G0, int... Gs>
-struct Dispatch<Sys, G0, Gs...> {
+template <class Sys, int D, int G0, int... Gs>
+struct Dispatch<Sys, D, G0, Gs...> {
   static cudaError_t launch(int prec, int G, int gpb, int grid, cudaStream_t s, const SolveArgs& a) {
     if (G == G0)
-      return prec == PREC_FP64 ? launch_one<Sys, double, G0>(gpb, grid, s, a)
-                               : launch_one<Sys, float, G0>(gpb, grid, s, a);
-    return Dispatch<Sys, Gs...>::launch(prec, G, gpb, grid, s, a);
+      return prec == PREC_FP64 ? launch_one<Sys, double, G0, D>(gpb, grid, s, a)
+                               : launch_one<Sys, float, G0, D>(gpb, grid, s, a);
+    return Dispatch<Sys, D, Gs...>::launch(prec, G, gpb, grid, s, a);
   }
   static cudaError_t occupancy(int prec, int G, int gpb, size_t* smem, int* bps) {
     if (G == G0)
-      return prec == PREC_FP64 ? occupancy_one<Sys, double, G0>(gpb, smem, bps)
-                               : occupancy_one<Sys, float, G0>(gpb, smem, bps);
-    return Dispatch<Sys, Gs...>::occupancy(prec, G, gpb, smem, bps);
+      return prec == PREC_FP64 ? occupancy_one<Sys, double, G0, D>(gpb, smem, bps)
+                               : occupancy_one<Sys, float, G0, D>(gpb, smem, bps);
+    return Dispatch<Sys, D, Gs...>::occupancy(prec, G, gpb, smem, bps);
+  }
+};
+
+constexpr int kDepth1 = 1, kDepth2 = 2;   // staging depths
+
+// a system whose groups stage one knot ahead only (SysOps.max_depth = 1)
+template <class Disp>
+struct DepthOne {
+  static cudaError_t launch(int prec, int G, int depth, int gpb, int grid, cudaStream_t s, const SolveArgs& a) {
+    return depth == 1 ? Disp::launch(prec, G, gpb, grid, s, a) : cudaErrorInvalidValue;
+  }
+  static cudaError_t occupancy(int prec, int G, int depth, int gpb, size_t* smem, int* bps) {
+    return depth == 1 ? Disp::occupancy(prec, G, gpb, smem, bps) : cudaErrorInvalidValue;
   }
 };
 

@@ -25,7 +25,7 @@ static int parse_arm7(const double* p, size_t np, std::vector<unsigned char>& bl
   return 0;
 }
 
-typedef Dispatch<SysArm7, 32> A7Dispatch;
+typedef Dispatch<SysArm7, kDepth1, 32> A7Dispatch;
 
 // the stored substep primals of one knot: n_sub of them (header [6], 0 means 1)
 static size_t arm7_knot_scratch(const double* p, size_t np, int prec) {
@@ -43,8 +43,9 @@ static SysOps make_ops() {
   o.default_gpb[0] = 2; o.default_gpb[1] = 2;
   o.accepts_actor = false;
   o.parse = parse_arm7;
-  o.launch = A7Dispatch::launch;
-  o.occupancy = A7Dispatch::occupancy;
+  o.max_depth = 1;
+  o.launch = DepthOne<A7Dispatch>::launch;
+  o.occupancy = DepthOne<A7Dispatch>::occupancy;
   o.knot_costs = knot_costs_one<SysArm7>;
   o.knot_scratch = arm7_knot_scratch;
   return o;

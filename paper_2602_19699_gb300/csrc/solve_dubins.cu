@@ -22,7 +22,7 @@ static int parse_dubins(const double* p, size_t np, std::vector<unsigned char>& 
   return 0;
 }
 
-typedef Dispatch<SysDubins, 1, 8, 16, 32> DBDispatch;
+typedef Dispatch<SysDubins, kDepth1, 1, 8, 16, 32> DBDispatch;
 
 static SysOps make_ops() {
   SysOps o{};
@@ -34,8 +34,9 @@ static SysOps make_ops() {
   o.default_gpb[0] = 8; o.default_gpb[1] = 8;
   o.accepts_actor = false;
   o.parse = parse_dubins;
-  o.launch = DBDispatch::launch;
-  o.occupancy = DBDispatch::occupancy;
+  o.max_depth = 1;
+  o.launch = DepthOne<DBDispatch>::launch;
+  o.occupancy = DepthOne<DBDispatch>::occupancy;
   o.knot_costs = knot_costs_one<SysDubins>;
   return o;
 }

@@ -42,7 +42,21 @@ static int parse_planar3(const double* p, size_t np, std::vector<unsigned char>&
   return 0;
 }
 
-typedef Dispatch<SysPlanar3, 1, 4, 8, 16, 32> P3Dispatch;
+typedef Dispatch<SysPlanar3, kDepth1, 1, 4, 8, 16, 32> P3Dispatch;
+
+// groups that stage two knots ahead (solve_planar3_d2.cu: its own translation
+// unit, so the two kernel sets compile in parallel)
+cudaError_t planar3_launch_d2(int prec, int G, int gpb, int grid, cudaStream_t s, const SolveArgs& a);
+cudaError_t planar3_occupancy_d2(int prec, int G, int gpb, size_t* smem, int* bps);
+
+static cudaError_t planar3_launch(int prec, int G, int depth, int gpb, int grid, cudaStream_t s, const SolveArgs& a) {
+  if (depth == 2) return planar3_launch_d2(prec, G, gpb, grid, s, a);
+  return depth == 1 ? P3Dispatch::launch(prec, G, gpb, grid, s, a) : cudaErrorInvalidValue;
+}
+static cudaError_t planar3_occupancy(int prec, int G, int depth, int gpb, size_t* smem, int* bps) {
+  if (depth == 2) return planar3_occupancy_d2(prec, G, gpb, smem, bps);
+  return depth == 1 ? P3Dispatch::occupancy(prec, G, gpb, smem, bps) : cudaErrorInvalidValue;
+}
 
 // every knot's stored derivative block (both precisions)
 static size_t planar3_knot_scratch(const double*, size_t, int) { return SysPlanar3::kDerivStride; }
@@ -58,8 +72,9 @@ static SysOps make_ops() {
   o.default_gpb[0] = 8; o.default_gpb[1] = 8;
   o.accepts_actor = false;
   o.parse = parse_planar3;
-  o.launch = P3Dispatch::launch;
-  o.occupancy = P3Dispatch::occupancy;
+  o.max_depth = 2;   // groups of 4 or more lanes
+  o.launch = planar3_launch;
+  o.occupancy = planar3_occupancy;
   o.knot_costs = knot_costs_one<SysPlanar3>;
   o.knot_scratch = planar3_knot_scratch;
   return o;

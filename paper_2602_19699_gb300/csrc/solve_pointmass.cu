@@ -21,7 +21,7 @@ static int parse_pointmass(const double* p, size_t np, std::vector<unsigned char
   return 0;
 }
 
-typedef Dispatch<SysPointMass, 1, 8, 16, 32> PMDispatch;
+typedef Dispatch<SysPointMass, kDepth1, 1, 8, 16, 32> PMDispatch;
 
 static SysOps make_ops() {
   SysOps o{};
@@ -33,8 +33,9 @@ static SysOps make_ops() {
   o.default_gpb[0] = 8; o.default_gpb[1] = 8;
   o.accepts_actor = false;
   o.parse = parse_pointmass;
-  o.launch = PMDispatch::launch;
-  o.occupancy = PMDispatch::occupancy;
+  o.max_depth = 1;
+  o.launch = DepthOne<PMDispatch>::launch;
+  o.occupancy = DepthOne<PMDispatch>::occupancy;
   o.knot_costs = knot_costs_one<SysPointMass>;
   return o;
 }

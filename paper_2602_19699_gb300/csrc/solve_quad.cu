@@ -30,7 +30,7 @@ static int parse_quad(const double* p, size_t np, std::vector<unsigned char>& bl
   return 0;
 }
 
-typedef Dispatch<SysQuad, 64, 32> QDispatch;
+typedef Dispatch<SysQuad, kDepth1, 64, 32> QDispatch;
 
 // the stored substep primals of one knot: n_sub of them (header [6], 0 means 1)
 static size_t quad_knot_scratch(const double* p, size_t np, int prec) {
@@ -49,8 +49,9 @@ static SysOps make_ops() {
   o.default_gpb[0] = 1; o.default_gpb[1] = 1;
   o.accepts_actor = true;
   o.parse = parse_quad;
-  o.launch = QDispatch::launch;
-  o.occupancy = QDispatch::occupancy;
+  o.max_depth = 1;
+  o.launch = DepthOne<QDispatch>::launch;
+  o.occupancy = DepthOne<QDispatch>::occupancy;
   o.knot_costs = knot_costs_one<SysQuad>;
   o.knot_scratch = quad_knot_scratch;
   return o;

@@ -3,7 +3,7 @@
 A child process loads ``libto_checked.so``, in which every computed index of
 the solver kernel is checked against the buffer it addresses, and runs small
 solves down every path: both precisions, every group size of the planar arm
-(1, 4, 8, 16, 32 lanes), horizons from 1 to T_max in one batch, the
+(1, 4, 8, 16, 32 lanes; staging depths 1 and 2), horizons from 1 to T_max in one batch, the
 Levenberg-Marquardt variant, forced step sequences, a caller's warm start,
 V_x and gains, the point mass, the Dubins car, the 7-DoF arm, the quadruped
 (64 and 32 lanes), one launch over several systems, the no-allocation entry
@@ -55,6 +55,10 @@ def _cases(P, W):
             s = P.Solver(prob, T_max=T_max, prec=prec, group_lanes=G)
             r = s.solve(b.x0, b.T, max_iter=15)
             keep(f"planar_{_pn(P, prec)}_{G}", r, s.problem)
+        for G in (4, 8, 16, 32):          # staging depth 2: records fetched two knots ahead
+            s = P.Solver(prob, T_max=T_max, prec=prec, group_lanes=G, stage_depth=2)
+            r = s.solve(b.x0, b.T, max_iter=15)
+            keep(f"planar_{_pn(P, prec)}_{G}_d2", r, s.problem)
     # Levenberg-Marquardt, forced steps, a caller's warm start, V_x
     s = P.Solver(prob, T_max=T_max, prec=P.TO_MIXED, reg=P.TO_REG_LM)
     keep("planar_lm", s.solve(b.x0, b.T, max_iter=15), s.problem)

@@ -151,6 +151,7 @@ def test_totune_persisted_choice(P, tmp_path, monkeypatch):
     assert len(rows) >= 4
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and lines[0].split()[1:3] == [str(opts.group_lanes), str(opts.groups_per_block)]
+    assert lines[0].split()[4] == str(opts.stage_depth) == "1"     # the point mass stages one knot ahead
     # a new problem handle, the same workload: the stored shape, no timing
     h2 = P.tocreate_problem(prob.sys, prob.params, 50)
     opts2 = P.to_default_opts(prec=P.TO_MIXED, max_iter=3)
