@@ -336,8 +336,107 @@ struct Solver {
         for (int j = 0; j <= i; ++j) Lf[i * m + j] = (R)L[i * m + j];
     return flag;
   }
-  TO_DEV static void chol_group(W& w, bool lm, double mu_lm) {
-    w.flag = factor(w.Quu, w.Quf, lm, mu_lm, w.L, w.Lf, w.mu);
+  // ------------------------------------------------------------------------
+  // The float64 factor of Q_uu spread over the 32 lanes of a warp (groups of
+  // whole warps).  Lane l holds the lower-triangle entries t = l + 32 e
+  // (row-major, diagonal included) in registers; step k of the right-looking
+  // elimination takes the pivot from its owner by a shuffle, scales column k
+  // (the diagonal keeps 1 / L_kk), publishes it in Lm (shared) and
+  // subtracts l_ik l_jk from every entry (i, j) with j > k.  Each entry thus
+  // takes exactly the operations of chol()'s sums, in the same order
+  // k = 0, 1, ..., so the factor is the one-lane factor's; the difference is
+  // that the m^3/3 multiply-adds of a step issue as one warp instruction per
+  // register slot.  kSeeded (mixed mode, where the factor is rounded to
+  // float32 for the solves): reciprocal roots from rsqrt_newton for pivots
+  // in the normal float32 range, else rsqrt.  Returns whether every pivot
+  // passed d > delta (the same on every lane).
+  // ------------------------------------------------------------------------
+  static constexpr int kTri = m * (m + 1) / 2, kTriSlots = (kTri + 31) / 32;
+  template <bool kSeeded>
+  TO_DEV static bool chol_warp_try(const double* Q, double* Lm, double shift, double delta, const int (&ri)[kTriSlots],
+                                   const int (&ci)[kTriSlots]) {
+    double a[kTriSlots];
+#pragma unroll
+    for (int e = 0; e < kTriSlots; ++e) {
+      a[e] = ri[e] >= 0 ? Q[ri[e] * m + ci[e]] : 0.0;
+      if (ri[e] >= 0 && ri[e] == ci[e]) a[e] += shift;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      const int tkk = k * (k + 1) / 2 + k;                  // compile-time once the loop unrolls
+      const double d = __shfl_sync(0xffffffffu, a[tkk / 32], tkk % 32);
+      ok = ok & dgt_nonneg(d, delta);
+      double r;
+      if (kSeeded) {
+        const long long bits = __double_as_longlong(d);
+        if (bits >= 0x3810000000000000LL && bits <= 0x47efffffe0000000LL) r = rsqrt_newton(d);   // FLT_MIN .. FLT_MAX
+        else r = rsqrt(d);
+      } else {
+        r = rsqrt(d);
+      }
+#pragma unroll
+      for (int e = 0; e < kTriSlots; ++e)
+        if (ci[e] == k) {
+          const double v = ri[e] == k ? r : a[e] * r;
+          a[e] = v;
+          Lm[ri[e] * m + k] = v;
+        }
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < kTriSlots; ++e)
+        if (ci[e] > k) a[e] -= Lm[ri[e] * m + k] * Lm[ci[e] * m + k];
+    }
+    return ok;
+  }
+  // factor() with chol_warp_try, run by the 32 lanes of the group's first
+  // warp; the flags, mu schedule and float rounding of the factor are
+  // factor()'s.  Writes w.L, w.Lf, w.flag and w.mu.
+  TO_DEV static void chol_warp(W& w, bool lm, double mu_lm, int lane) {
+    constexpr bool kSeed = sizeof(R) == 4;
+    int ri[kTriSlots], ci[kTriSlots];
+#pragma unroll
+    for (int e = 0; e < kTriSlots; ++e) {
+      const int t = lane + 32 * e;
+      int i = 0;
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;               // row of entry t (t < kTri: i < m)
+      ri[e] = t < kTri ? i : -1;
+      ci[e] = t < kTri ? t - i * (i + 1) / 2 : -1;
+    }
+    R mxr = R(0);
+#pragma unroll
+    for (int i = 0; i < m; ++i) mxr = max_abs(mxr, w.Quf[i * m + i]);
+    const double mx = (double)mxr;
+    int flag;
+    double mu;
+    if (lm) {
+      mu = mu_lm;
+      flag = 3;
+      if (isfinite(mx) && chol_warp_try<kSeed>(w.Quu, w.L, mu, 1e-12 * (mx + mu), ri, ci)) flag = 0;
+    } else {
+      mu = 0;
+      flag = 2;
+      if (mx > 0 && isfinite(mx)) {
+        const double delta = 1e-12 * mx;
+        if (chol_warp_try<kSeed>(w.Quu, w.L, 0.0, delta, ri, ci)) {
+          flag = 0;
+        } else {
+          double mt = 1e-6 * mx;
+          for (int t = 0; t < 40; ++t) {
+            if (chol_warp_try<kSeed>(w.Quu, w.L, mt, delta, ri, ci)) { flag = 1; mu = mt; break; }
+            mt *= 10.0;
+          }
+        }
+      }
+    }
+    if (flag < 2)
+#pragma unroll
+      for (int e = 0; e < kTriSlots; ++e)
+        if (ri[e] >= 0) w.Lf[ri[e] * m + ci[e]] = (R)w.L[ri[e] * m + ci[e]];
+    if (lane == 0) {
+      w.flag = flag;
+      w.mu = mu;
+    }
   }
 
   // x = (L L^T)^{-1} b with L's diagonal stored as reciprocals
@@ -855,9 +954,7 @@ struct Solver {
         }
       g.sync();
       TO_TICK(2);
-      if (act && g.lane == 0) {
-        chol_group(w, a.lm, mu_lm);
-      }
+      if (act && g.lane < 32) chol_warp(w, a.lm, mu_lm, g.lane);   // act is uniform over the group
       g.sync();
     const int flag = act ? w.flag : 0;
     if (act && flag < 2)

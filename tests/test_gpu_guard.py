@@ -17,7 +17,9 @@ conditioned (the oracle itself moves by less than 1e-12 when x0 moves by
 1e-15), and both set TO_ST_FLAG_REG.  The replay is the first iteration,
 where every knot is regularised whatever the rounding; in FP64 the gains of
 the backward pass at the new iterate (where the last knot is regularised)
-are compared too.
+are compared too.  The replay runs with 8-lane groups (the sub-warp
+factor, on every lane) and with whole-warp groups (the factor spread over
+the warp's lanes, one lower-triangle entry per lane).
 
 Tolerances.  Whenever the guard fires, the failing pivot is far below mu, so
 Q_uu + mu I has a condition number of about max|diag| / mu = 1e6 (the shift
@@ -72,8 +74,9 @@ def _oracle_replay(o, b, iters, forced, want_K):
     return r1, kx, kk
 
 
+@pytest.mark.parametrize("lanes", [8, 32])       # sub-warp groups, and a whole warp (the lane-parallel factor)
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_guard_replay(P, oracle_mod, prec):
+def test_guard_replay(P, oracle_mod, prec, lanes):
     prob = _problem()
     b = W.make_batch(prob, 16, seed=3, T=(20, 40))
     o = oracle_mod.Oracle.from_problem(prob)
@@ -83,7 +86,8 @@ def test_guard_replay(P, oracle_mod, prec):
     fp64 = prec == "fp64"
     ro, kx, kk = _oracle_replay(o, b, iters, ro0["alpha_hist"], want_K=fp64)
     assert np.all(ro["status"] & FLAG_REG)
-    s = P.Solver(prob, T_max=40, prec=P.TO_FP64 if fp64 else P.TO_MIXED)
+    s = P.Solver(prob, T_max=40, prec=P.TO_FP64 if fp64 else P.TO_MIXED, group_lanes=lanes,
+                 groups_per_block=64 // lanes)
     want = ("X", "U", "K") if fp64 else ("X", "U")
     rg = s.solve(b.x0, b.T, forced_alpha=ro0["alpha_hist"], max_iter=iters, want_vx=1 if fp64 else 0, want=want)
     np.testing.assert_array_equal(rg["iters"], ro["iters"])

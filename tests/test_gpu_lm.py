@@ -28,15 +28,17 @@ def _sensitivity_lm(o, b, ro, max_iter):
     return k
 
 
+@pytest.mark.parametrize("lanes", [8, 32])       # sub-warp groups, and a whole warp (the lane-parallel factor)
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_planar3_lm_replay(P, oracle_mod, prec):
+def test_planar3_lm_replay(P, oracle_mod, prec, lanes):
     prob = W.planar3(seed=1)
     b = W.make_batch(prob, 24, seed=2, T=(20, 40))
     o = oracle_mod.Oracle.from_problem(prob)
     iters = 8
     ro = o.solve(b.x0, b.T, max_iter=iters, tol=1e-8, n_alpha=16, reg="lm")
     kappa = _sensitivity_lm(o, b, ro, iters)
-    s = P.Solver(prob, T_max=40, prec=P.TO_FP64 if prec == "fp64" else P.TO_MIXED, reg=P.TO_REG_LM)
+    s = P.Solver(prob, T_max=40, prec=P.TO_FP64 if prec == "fp64" else P.TO_MIXED, reg=P.TO_REG_LM,
+                 group_lanes=lanes, groups_per_block=64 // lanes)
     rg = s.solve(b.x0, b.T, forced_alpha=ro["alpha_hist"], max_iter=iters)
     well = _check(ro, rg, kappa, prec, b.T)
     assert well.sum() >= 4
