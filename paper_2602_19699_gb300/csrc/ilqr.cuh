@@ -1620,7 +1620,7 @@ struct Solver {
             }
             if constexpr (Sys::template kGroupStep<G>) {
               // the system's step is shared by partner lanes (group barriers inside;
-              // act is uniform over a CTA-wide group)
+              // act is uniform over the group)
               const R l = Sys::template cost_step_group<R, G>(P, g, act && mine, xh, xlo, uh, w.sx);
               if (act && mine) Jc.add(l);
             }

@@ -44,7 +44,7 @@ static SysOps make_ops() {
   fill_layout<SysQuad>(o);
   o.n_groups = 2;
   o.groups[0] = 64;   // a candidate lane's partner on the other warp factors the mass matrix
-  o.groups[1] = 32;   // one warp per instance, each candidate lane steps alone
+  o.groups[1] = 32;   // one warp per instance: the partner is the candidate lane + 16
   o.default_G = 64;
   o.default_gpb[0] = 1; o.default_gpb[1] = 1;
   o.accepts_actor = true;

@@ -620,9 +620,11 @@ struct SysRigid {
   template <class R, int G>
   TO_DEV static R cost_step_group(const ParamsT<R>& P, const Group<G>& g, bool mine, R* xh, R* xl, const R* u,
                                   R* scratch) {
-    static_assert(kGroupStep<G>, "a partner lane on the other warp");
+    static_assert(kGroupStep<G>, "a partner lane in the group's other half");
+    constexpr int H = G / 2;                  // candidate c's partner is lane c + H
+    static_assert(H >= kStepSlots, "a partner for every candidate slot");
     const int c = g.lane;
-    const int slot = c < 32 ? c : c - 32;
+    const int slot = c < H ? c : c - H;
     R* sq = scratch + slot * kStepSlot;       // q of the candidate's substep
     R* sL = sq + N;                           // the factor of M(q)
     R* flag = scratch + kStepSlots * kStepSlot;
@@ -645,7 +647,7 @@ struct SysRigid {
 #pragma unroll
         for (int i = 0; i < N; ++i) z[i] = R(0);
         rnea<R, R>(P, xh, xh + N, z, true, KIND == RK_QUAD, hb);
-      } else if (c >= 32 && slot < kStepSlots && flag[slot] != R(0)) {
+      } else if (c >= H && slot < kStepSlots && flag[slot] != R(0)) {
         mass_chol_mem(P, sq, sL);
       }
       g.sync();
@@ -773,18 +775,19 @@ struct SysRigid {
   // elements per stored substep primal (a whole number of 16-byte chunks)
   template <class R> static constexpr int kPrimStride = (int)(((sizeof(Prim<R>) + 15) / 16 * 16) / sizeof(R));
 
-  // Line search of a 64-lane group: candidate lane c < kStepSlots steps its
-  // rollout with lane c + 32 (the other warp) as its partner, which forms and
+  // Line search of a group of whole warps: candidate lane c < kStepSlots
+  // steps its rollout with lane c + G/2 as its partner (the other warp of a
+  // 64-lane group, the other half-warp of a 32-lane one), which forms and
   // factors the mass matrix while lane c runs the bias Newton-Euler pass.
   // Per candidate the scratch holds its substep's q and the factor.
-  template <int G> static constexpr bool kGroupStep = (KIND == RK_QUAD) && G >= 64;
+  template <int G> static constexpr bool kGroupStep = G >= 32;
   static constexpr int kStepSlots = 16, kStepSlot = N + N * N;
   // the group's shared-memory scratch (the solver reserves it in its work
   // area): the derivative primal, or the line search's per-candidate slots
   template <class R>
   struct Scratch {
     static constexpr int prim = 2 * kPrimStride<R>;   // the staged substep primals, double-buffered
-    static constexpr int step = KIND == RK_QUAD ? kStepSlots * kStepSlot + kStepSlots : 0;
+    static constexpr int step = kStepSlots * kStepSlot + kStepSlots;
     static constexpr int elems = prim > step ? prim : step;
   };
 
