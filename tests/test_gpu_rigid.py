@@ -60,9 +60,10 @@ def test_arm7_replay(P, oracle_mod, prec):
 def test_quad_replay(P, oracle_mod, prec, lanes):
     # six short replays: the oracle's sensitivity to a 1e-15 move of x0 is
     # 4e-15 .. 6e-14 here, so at least two instances take the strict mixed
-    # bounds (kappa < 1e-14) and all take the FP64 one.  64 lanes: a partner
-    # lane on the other warp factors each candidate's mass matrix; 32 lanes:
-    # each candidate steps alone and the 48 tangent directions take two passes
+    # bounds (kappa < 1e-14) and all take the FP64 one.  Each candidate's
+    # partner lane factors its mass matrix: lane c + 32 (the other warp) at
+    # 64 lanes, lane c + 16 at 32 lanes, where the 48 tangent directions also
+    # take two passes
     prob = W.quad(seed=2, with_actor=False)
     b = W.make_batch(prob, 6, seed=1, T=6)
     o = oracle_mod.Oracle.from_problem(prob)
