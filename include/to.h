@@ -173,8 +173,9 @@ typedef struct {
   size_t hbm_budget_bytes;/* 0 = no limit; else tocreate_batch / tosolve_batch
                              refuse a workspace larger than this (TO_ERR_BUDGET) */
   int group_lanes;        /* threads per instance, one of the system's supported
-                             sizes (1/8/16/32 point mass, planar arm and
-                             Dubins car, 32 arm, 64 quadruped); 0 = the totune
+                             sizes (1/8/16/32 point mass and Dubins car,
+                             1/4/8/16/32 planar arm, 32 arm, 64/32
+                             quadruped); 0 = the totune
                              choice, else the system's default.  1: one thread
                              per instance with every per-knot matrix in
                              registers; its line search tries one step size
