@@ -89,3 +89,29 @@ def test_parser_rejects_other_joint_trees(libto, case):
     with pytest.raises(P.ToError) as e:
         P.tocreate_problem(prob.sys, p, 20)
     assert e.value.code == P.TO_ERR_ARG
+
+
+def _struct_fields(name):
+    """Field names, in order, of a typedef struct { ... } name; in include/to.h."""
+    src = open(os.path.join(ROOT, "include", "to.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "int a, b" / "const double* p" / "size_t n": names after the type
+        names = decl.split(None, 1)[1] if not decl.startswith("const ") else decl.split(None, 2)[2]
+        for part in names.split(","):
+            fields.append(part.strip().lstrip("*").strip())
+    return fields
+
+
+@pytest.mark.parametrize("name", ["to_problem_desc", "to_solver_opts", "to_tune_row"])
+def test_binding_structs_mirror_the_header(libto, name):
+    """The ctypes structs of the binding list the header's fields in the
+    header's order (a drift would silently shift every later field)."""
+    py = [f for f, _ in getattr(libto, name)._fields_]
+    assert py == _struct_fields(name)
