@@ -775,19 +775,21 @@ struct SysRigid {
   // elements per stored substep primal (a whole number of 16-byte chunks)
   template <class R> static constexpr int kPrimStride = (int)(((sizeof(Prim<R>) + 15) / 16 * 16) / sizeof(R));
 
-  // Line search of a group of whole warps: candidate lane c < kStepSlots
+  // Line search of the quadruped's groups: candidate lane c < kStepSlots
   // steps its rollout with lane c + G/2 as its partner (the other warp of a
   // 64-lane group, the other half-warp of a 32-lane one), which forms and
   // factors the mass matrix while lane c runs the bias Newton-Euler pass.
-  // Per candidate the scratch holds its substep's q and the factor.
-  template <int G> static constexpr bool kGroupStep = G >= 32;
+  // Per candidate the scratch holds its substep's q and the factor.  The
+  // 7-DoF arm's candidates step alone: its 7-body mass matrix is cheap, and
+  // the partner split measured 2 % slower there in mixed mode.
+  template <int G> static constexpr bool kGroupStep = (KIND == RK_QUAD) && G >= 32;
   static constexpr int kStepSlots = 16, kStepSlot = N + N * N;
   // the group's shared-memory scratch (the solver reserves it in its work
   // area): the derivative primal, or the line search's per-candidate slots
   template <class R>
   struct Scratch {
     static constexpr int prim = 2 * kPrimStride<R>;   // the staged substep primals, double-buffered
-    static constexpr int step = kStepSlots * kStepSlot + kStepSlots;
+    static constexpr int step = KIND == RK_QUAD ? kStepSlots * kStepSlot + kStepSlots : 0;
     static constexpr int elems = prim > step ? prim : step;
   };
 
